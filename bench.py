@@ -1,0 +1,271 @@
+"""Benchmark: SSN solves to ||R(w)|| <= 1e-6 per second on GB300 (features + Algorithm 2 per step).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--workload NAME] [--precision fp64|mixed]
+
+A step is one pass of the whole hot path on one synthetic problem: feature assembly (kernel
+embeddings, Gram matrices, Cholesky) followed by Algorithm 2 until the natural residual is at
+most 1e-6.  Under torchrun every rank solves its own independently seeded problem of the same
+shape (weak scaling, no collective on the data path).  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2310_14087_gb300 import workloads  # noqa: E402
+
+METRIC = "SSN solves/s to ||R||<=1e-6 (time-to-residual = ms_per_step), FP64 vs mixed"
+WORKLOADS = {
+    # BASELINE shapes in the Sec. 5 parameter regime (sigma^2 = 0.005, lambda1 = 1/l,
+    # lambda2 = 1/sqrt(n), unit-cube filling points)
+    "paper_d5_n1000_l300": dict(d=5, n=1000, l=300),
+    "paper_d2_n100_l50": dict(d=2, n=100, l=50),
+    "paper_d10_n2000_l1024": dict(d=10, n=2000, l=1024),
+}
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12     # SMs x FP64 FMA/clk x 2 flops x max clock
+
+
+def make_problem(name: str, rank: int):
+    cfg = WORKLOADS[name]
+    return workloads.paper_regime(seed=1 + 1000 * rank, d=cfg["d"], n=cfg["n"], l=cfg["l"])
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def oracle_solve(p):
+    from oracle import kot_oracle as ko
+    t = time.perf_counter()
+    F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
+    r = ko.ssn_solve(F, p.tol)
+    return time.perf_counter() - t, r
+
+
+def run_reference(args, rank, world):
+    """The oracle (plain FP64 NumPy/LAPACK) timed on the host cores: rank 0 only."""
+    if rank != 0:
+        return
+    p = make_problem(args.workload, 0)
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle_solve(p)
+    times = []
+    iters = None
+    for _ in range(args.steps):
+        t, r = oracle_solve(p)
+        times.append(t)
+        iters = r.iters
+    total = sum(times)
+    cores = len(os.sched_getaffinity(0))
+    val = args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, **WORKLOADS[args.workload], "tol": 1e-6,
+                   "oracle_iters": iters},
+        "cpu_baseline": {"value": val, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} full solves (features + Algorithm 2 to 1e-6) of "
+                                   f"{args.workload}, NumPy/LAPACK with default BLAS threads"},
+        "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="paper_d5_n1000_l300", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2310_14087_gb300 import kot
+
+    torch.cuda.set_device(local_rank)
+    dev = f"cuda:{local_rank}"
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(dev))
+    p = make_problem(args.workload, rank)
+    dp = kot.DeviceProblem.from_problem(p, dev)
+    stream = torch.cuda.Stream(device=dev)
+    prec = kot.FP64 if args.precision == "fp64" else kot.MIXED
+    ctx = kot.Context(device=local_rank, stream=stream.cuda_stream, precision=prec)
+    g = torch.zeros(p.l, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2
+
+    def step():
+        ctx.build_features(dp.X, dp.Y, dp.Xf, dp.Yf, p.sigma, p.lambda1, p.lambda2)
+        return ctx.ssn_solve(p.tol, g)
+
+    for _ in range(args.warmup):
+        res = step()
+
+    # ---- timed region: inputs resident in HBM; L2 flushed before every step (untimed)
+    peaks = load_peaks()
+    ctx.profile((1 << len(kot.KERNEL_CLASSES)) - 1)
+    launches0 = kot.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    iters = []
+    with ClockSampler(local_rank) as clocks:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+            res = step()
+            with torch.cuda.stream(stream):
+                ev[k][1].record(stream)
+            iters.append(res.iters)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = kot.launch_count() - launches0
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    stats = {name: ctx.profile_read(i) for i, name in enumerate(kot.KERNEL_CLASSES)}
+    ctx.profile(0)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * args.steps / (ms_max / 1e3)
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    hctx = kot.Context(device=local_rank, host_pointers=1, precision=prec)
+    hX, hY, hXf, hYf = (np.ascontiguousarray(a, dtype=np.float64) for a in (p.X, p.Y, p.Xf, p.Yf))
+    hg = np.zeros(p.l)
+    for _ in range(1):
+        hctx.build_features(hX, hY, hXf, hYf, p.sigma, p.lambda1, p.lambda2)
+        hctx.ssn_solve(p.tol, hg)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        hctx.build_features(hX, hY, hXf, hYf, p.sigma, p.lambda1, p.lambda2)
+        hres = hctx.ssn_solve(p.tol, hg)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * args.steps / float(t.item())
+    h2d = 8 * (hX.size + hY.size + hXf.size + hYf.size)
+    d2h = 8 * p.l
+
+    if rank == 0:
+        # dominant kernel class by device time inside the timed region
+        dom = max(stats, key=lambda k: stats[k].ms)
+        s = stats[dom]
+        per_launch_ms = s.ms / max(1, s.launches)
+        achieved = (s.flops / max(1, s.launches)) / (per_launch_ms * 1e-3) / 1e12
+        roofline = {"kernel": dom, "bound": "alu", "achieved": achieved,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "traffic": None, "launches": s.launches, "avg_launch_us": per_launch_ms * 1e3,
+                    "share_of_step": s.ms / ms, "peak_source": "FP64 FMA: 152 SMs x 2/clk x 2.07 GHz"}
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, **WORKLOADS[args.workload], "tol": 1e-6,
+                       "precision": args.precision, "iters_per_solve": iters[-1],
+                       "l2": "flushed before every step (256 MB write, untimed)"},
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+            "roofline": roofline,
+            "kernels": {k: {"launches": v.launches, "ms": v.ms} for k, v in stats.items()},
+        }
+        if not args.no_cpu_baseline and world == 1:
+            tcpu, r = oracle_solve(p)
+            line["cpu_baseline"] = {
+                "value": 1.0 / tcpu, "unit": "solves/s", "cores": len(os.sched_getaffinity(0)),
+                "kind": "oracle",
+                "sample": f"1 full solve of {args.workload} (features + Algorithm 2, {r.iters} iterations), "
+                          "NumPy/LAPACK FP64, default BLAS threads"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

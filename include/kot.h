@@ -1,0 +1,180 @@
+/*
+ * kot.h -- C ABI of the GB300 library for the specialized semismooth Newton (SSN) method for
+ * kernel-based optimal transport (Lin, Cuturi & Jordan).
+ *
+ * Notation: n = samples per measure (the paper's n_sample), l = filling points (the paper's n),
+ * d = dimension of x and of y.  All matrices are row-major, contiguous, FP64.
+ *
+ * Pointers: every array argument is a DEVICE pointer (CUDA global memory of the context's
+ * device) unless the context was created with kot_options.host_pointers = 1, in which case every
+ * array argument is HOST memory and the library copies it in and out on its stream inside the
+ * call.  The caller owns all argument arrays; the context owns every internal buffer and frees
+ * them in kot_destroy.  Calls are stream-ordered on kot_options.stream and return after that
+ * stream has finished the call's work (outputs are ready on return).
+ *
+ * Errors: every entry point returns a kot_status.  Arguments are validated before any GPU work
+ * (KOT_ERR_INVALID leaves the context unchanged).  kot_last_error() gives a one-line reason.
+ * No entry point aborts the process, and no kernel waits without an iteration bound.
+ *
+ * Threads: a context is used by one host thread at a time.
+ */
+#ifndef KOT_H
+#define KOT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kot_ctx kot_ctx;
+
+typedef enum {
+  KOT_OK = 0,
+  KOT_ERR_INVALID = 1,        /* bad argument; nothing was launched                      */
+  KOT_ERR_CUDA = 2,           /* a CUDA runtime call failed                              */
+  KOT_ERR_OOM = 3,            /* device allocation failed                                */
+  KOT_ERR_NOT_PD = 4,         /* Cholesky of K + eps I failed up to the jitter limit      */
+  KOT_ERR_NO_CONVERGENCE = 5, /* iteration cap reached; outputs hold the last iterate    */
+  KOT_ERR_NONFINITE = 6,      /* NaN/Inf met in the iteration                            */
+  KOT_ERR_TIMEOUT = 7,        /* a bounded device wait gave up                           */
+  KOT_ERR_STATE = 8           /* call order: e.g. solve before features                  */
+} kot_status;
+
+typedef enum {
+  KOT_FP64 = 0,       /* every step in FP64                                             */
+  KOT_MIXED = 1       /* FP64 features/residual/stop test; FP32 eigen-solve with FP64
+                         refinement; reduced-precision Jacobian products inside CG         */
+} kot_precision;
+
+/* Algorithm constants.  Defaults (kot_default_options): the values of Sec. 5 for alpha1,
+ * alpha2, beta0, beta1, beta2; CG cap 20 (Sec. 4.4 remark); tau = 0.1, kappa = 1,
+ * theta0 = 1, theta_min = 1e-6, theta_max = 1e6, eg_step = 0 (use 1/L), jitter = 1e-10,
+ * jitter_max = 1e-6, max_iter = 200. */
+typedef struct {
+  int device;              /* CUDA device ordinal                                        */
+  void* stream;            /* cudaStream_t to order work on; NULL = a stream of its own   */
+  int precision;           /* kot_precision                                              */
+  int host_pointers;       /* 1: array arguments are host memory (see above)             */
+  int max_iter;            /* outer iterations of Algorithm 2                            */
+  int cg_max_iter;         /* CG iterations per Newton direction                         */
+  double tau, kappa;       /* inexact Newton test, Eq. (4.3)                              */
+  double alpha1, alpha2;   /* theta rule thresholds (Sec. 4.3)                           */
+  double beta0, beta1, beta2;
+  double theta0, theta_min, theta_max;
+  double eg_step;          /* <= 0: 1/L, L = max rowsum|Q|/(2 l2) + sqrt(max rowsum (Kt o Kt)) */
+  double jitter;           /* eps = jitter * max_i K_ii, x10 on failure ...              */
+  double jitter_max;       /* ... up to jitter_max * max_i K_ii                          */
+  int use_eg;              /* 1: Algorithm 2 with the EG safeguard; 0: plain SSN steps   */
+  int record_history;      /* 1: keep ||R(w_k)|| per iteration (kot_get_history)         */
+} kot_options;
+
+typedef struct {
+  int status;              /* kot_status of the solve                                    */
+  int iters, ssn_accepted, eg_taken, cg_total;
+  double residual;         /* ||R(w)|| = ||r1||_2 + ||r2||_F at the returned iterate      */
+  double r1_norm, r2_norm;
+  double objective;        /* dual objective of Eq. (3.3) at gamma                       */
+  double ot_hat;           /* estimator OT-hat (Sec. 3)                                  */
+  double eps;              /* Cholesky jitter used                                       */
+  double seconds;          /* wall time of the call                                      */
+} kot_result;
+
+/* Fill *opt with the defaults listed above.  Returns KOT_ERR_INVALID if opt is NULL. */
+kot_status kot_default_options(kot_options* opt);
+
+/* Create a context on opt->device (opt NULL = defaults).  *out receives the handle. */
+kot_status kot_create(kot_ctx** out, const kot_options* opt);
+
+/* Release every buffer of the context.  NULL is accepted. */
+kot_status kot_destroy(kot_ctx* ctx);
+
+/* One-line description of the last error of this context (never NULL). */
+const char* kot_last_error(const kot_ctx* ctx);
+
+/* Feature assembly (Sec. 3, definitions following Eq. (3.2)):
+ *   w_mu(xf_i) = (1/n) sum_j k(x_j, xf_i),  w_nu(yf_i) = (1/n) sum_j k(y_j, yf_i),
+ *   q2 = (1/n^2) sum_ij k(x_i, x_j) + (1/n^2) sum_ij k(y_i, y_j),
+ *   Q_ij = k(xf_i, xf_j) + k(yf_i, yf_j),  c_i = ||xf_i - yf_i||^2,
+ *   z_i = w_mu(xf_i) + w_nu(yf_i) - lambda2 c_i,
+ *   K_ij = k((xf_i, yf_i), (xf_j, yf_j)),  R upper triangular with R^T R = K + eps I.
+ * k(a, b) = exp(-||a - b||^2 / (2 sigma^2)).
+ * X, Y: n x d.  Xf, Yf: l x d (the x and y halves of the filling pairs).
+ * Requires d, n, l >= 1 and sigma, lambda1, lambda2 > 0.  KOT_ERR_NOT_PD if K + eps I is not
+ * positive definite for eps up to jitter_max * max K_ii. */
+kot_status kot_build_features(kot_ctx* ctx, int d, int n, const double* X, const double* Y,
+                              int l, const double* Xf, const double* Yf, double sigma,
+                              double lambda1, double lambda2);
+
+/* Inject the dual problem data directly (Eq. (3.3)): Q (l x l, symmetric), z (l), q2, R (l x l,
+ * upper triangular, the rows below the diagonal are ignored).  w_mu + w_nu is taken as
+ * z (so ot_hat uses z); used for closed-form cases. */
+kot_status kot_set_features(kot_ctx* ctx, int l, const double* Q, const double* z, double q2,
+                            const double* R, double lambda1, double lambda2);
+
+/* Copy out the assembled features; any output pointer may be NULL.  Q, K, R: l x l; z, w_mu,
+ * w_nu, c: l; q2, eps: one double each. */
+kot_status kot_get_features(kot_ctx* ctx, double* Q, double* K, double* R, double* z,
+                            double* w_mu, double* w_nu, double* c, double* q2, double* eps);
+
+/* Natural residual map R(w) of Eq. (4.2) at w = (gamma, X):
+ *   r1 = (Q gamma - z)/(2 lambda2) - Phi(X),  Phi(X)_i = (R^T X R)_ii,
+ *   r2 = X - Pi_{S+}(X - (Phi*(gamma) + lambda1 I)),  Phi*(gamma) = R diag(gamma) R^T,
+ * with Pi_{S+} by spectral decomposition (Eq. (4.4)).  gamma: l; X: l x l symmetric.
+ * Outputs (any may be NULL): r1 (l), r2 (l x l), proj = Pi_{S+}(Z) (l x l), sig = eigenvalues
+ * of Z in ascending order (l), norms[3] = {||r1||_2, ||r2||_F, ||R(w)||}. */
+kot_status kot_residual(kot_ctx* ctx, const double* gamma, const double* X, double* r1,
+                        double* r2, double* proj, double* sig, double* norms);
+
+/* Regularised Newton direction of Eq. (4.2)-(4.3) by Algorithm 1 at w = (gamma, X) with
+ * regularisation mu > 0: CG on (Q/(2 lambda2) + mu I + Phi T Phi*) dgamma = a1 with the
+ * operator T_k of Sec. 4.3 (G + G^T form when |alpha| <= l/2, complement form otherwise).
+ * cg_tol_abs > 0 stops CG at ||residual||_2 <= cg_tol_abs (at most 10 l + 50 iterations);
+ * cg_tol_abs <= 0 uses the inexact test of Eq. (4.3) with the context's tau, kappa and
+ * cg_max_iter.  Outputs: dgamma (l), dX (l x l), cg_iters (host int, may be NULL). */
+kot_status kot_newton_direction(kot_ctx* ctx, const double* gamma, const double* X, double mu,
+                                double cg_tol_abs, double* dgamma, double* dX, int* cg_iters);
+
+/* Algorithm 2 from w0 = (gamma0, X0) (NULL = zeros) until ||R(w_k)|| <= tol or max_iter.
+ * gamma_out (l) is required; X_out (l x l) may be NULL; res may be NULL.
+ * Returns KOT_ERR_NO_CONVERGENCE at the cap with the last iterate in the outputs. */
+kot_status kot_ssn_solve(kot_ctx* ctx, double tol, double* gamma_out, double* X_out,
+                         const double* gamma0, const double* X0, kot_result* res);
+
+/* Residual history of the last solve (record_history = 1): copies min(cap, iters + 1) values
+ * of ||R(w_k)|| to the host array hist; *count receives the number copied. */
+kot_status kot_get_history(kot_ctx* ctx, double* hist, int cap, int* count);
+
+/* One problem of a batch.  Arrays follow the context's pointer mode. */
+typedef struct {
+  int d, n, l;
+  const double *X, *Y, *Xf, *Yf;
+  double sigma, lambda1, lambda2, tol;
+  double* gamma_out;       /* l, required */
+} kot_problem;
+
+/* Solve B independent problems (features + Algorithm 2 each).  res receives B results (host
+ * array).  Problems are run largest-first on the context's device.  The call returns the first
+ * non-OK status among the problems (KOT_OK if all converged); each res[i].status is per problem. */
+kot_status kot_batch_solve(kot_ctx* ctx, int B, const kot_problem* probs, kot_result* res);
+
+/* ---- tracing: per-kernel-class launch statistics (not part of the paper's method) ----
+ * Kernel classes: 0 FP64 GEMM tiles, 1 Jacobi rotation round, 2 Jacobi angles, 3 kernel mean
+ * embeddings, 4 embedding-norm pair sums, 5 Gram matrices Q and K, 6 Cholesky diagonal block.
+ * kot_profile(ctx, mask) turns on timing of the classes whose bit is set in mask (0 = off) and
+ * clears the statistics.  While on, every launch of an enabled class is bracketed by CUDA events
+ * on the context's stream.  kot_profile_read fills, for class cls, the number of launches, the
+ * summed event time in milliseconds, and the summed algorithmic flops and bytes of those
+ * launches (the counts each launch site states for its arithmetic and its compulsory traffic). */
+typedef struct {
+  long long launches;
+  double ms, flops, bytes;
+} kot_kernel_stats;
+
+kot_status kot_profile(kot_ctx* ctx, int mask);
+/* Total number of kernels this library has launched in the process so far (all contexts). */
+kot_status kot_launch_count(long long* out);
+kot_status kot_profile_read(kot_ctx* ctx, int cls, kot_kernel_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KOT_H */

@@ -1,0 +1,847 @@
+// C ABI of libkot and the host-side driver of Algorithm 2.  Every arithmetic step runs in the
+// kernels of dense.cu, features.cu, eig.cu and newton.cu; the host only sequences launches,
+// reads back the scalars that steer the iteration (norms, CG step lengths, the alpha split) and
+// applies the scalar rules of Algorithm 2 (theta update, acceptance, stopping).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "kot_internal.cuh"
+
+using namespace kot;
+
+namespace {
+
+struct EigSlot {
+  DevBuf<double> P, sig;
+  int nb = 0;          // number of eigenvalues <= 0 (alpha-bar); alpha = the last l - nb
+  bool valid = false;
+};
+
+struct ResState {
+  DevBuf<double> r1, r2;
+  double n1 = 0, n2 = 0, norm = 0;
+};
+
+__global__ void k_maxdiag(int l, const double* __restrict__ K, double* __restrict__ out) {
+  __shared__ double sh[256];
+  double m = -INFINITY;
+  for (int i = threadIdx.x; i < l; i += 256) m = fmax(m, K[(size_t)i * l + i]);
+  sh[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+}  // namespace
+
+struct kot_ctx {
+  kot_options opt{};
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::string err = "no error";
+  int l = 0;
+  bool have = false;
+  double lambda1 = 0, lambda2 = 0, q2 = 0, eps = 0, eg_L = 0;
+  DevBuf<double> Q, K, R, z, w_mu, w_nu, c;
+  DevBuf<double> stage[8];                     // host-pointer mode staging
+  DevBuf<double> g, X, vg, vX, tg, tX, dg, dX;
+  ResState rw, rv, rt;
+  EigSlot ew, ev, et, e1, e2;
+  DevBuf<double> M1, M2, M3, M4, M5, M6, TU, TV, TW, TG;
+  DevBuf<double> v1, v2, v3, v4, v5, v6;
+  DevBuf<double> partial, scal, bounds;
+  DevBuf<int> iscal;
+  double* hs = nullptr;                        // pinned host scalars
+  int* hi = nullptr;
+  JacobiWork jw;
+  std::vector<double> hist;
+  Profiler prof;
+};
+
+namespace {
+
+constexpr int kMaxSweeps = 40;
+
+void set_defaults(kot_options* o) {
+  std::memset(o, 0, sizeof(*o));
+  o->device = 0;
+  o->stream = nullptr;
+  o->precision = KOT_FP64;
+  o->host_pointers = 0;
+  o->max_iter = 200;
+  o->cg_max_iter = 20;
+  o->tau = 0.1;
+  o->kappa = 1.0;
+  o->alpha1 = 1e-6;
+  o->alpha2 = 1.0;
+  o->beta0 = 0.5;
+  o->beta1 = 1.2;
+  o->beta2 = 5.0;
+  o->theta0 = 1.0;
+  o->theta_min = 1e-6;
+  o->theta_max = 1e6;
+  o->eg_step = 0.0;
+  o->jitter = 1e-10;
+  o->jitter_max = 1e-6;
+  o->use_eg = 1;
+  o->record_history = 0;
+}
+
+bool pos_finite(double v) { return std::isfinite(v) && v > 0.0; }
+
+void fail(kot_status s, const std::string& what) { throw Error{s, what}; }
+
+// ------------------------------------------------------------------ buffers and I/O
+void ensure(kot_ctx* C, int l) {
+  const size_t L2 = (size_t)l * l, L = (size_t)l;
+  for (DevBuf<double>* b : {&C->Q, &C->K, &C->R, &C->X, &C->vX, &C->tX, &C->dX, &C->M1, &C->M2,
+                            &C->M3, &C->M4, &C->M5, &C->M6, &C->TU, &C->TV, &C->TW, &C->TG,
+                            &C->rw.r2, &C->rv.r2, &C->rt.r2})
+    b->alloc(L2);
+  for (DevBuf<double>* b : {&C->z, &C->w_mu, &C->w_nu, &C->c, &C->g, &C->vg, &C->tg, &C->dg,
+                            &C->v1, &C->v2, &C->v3, &C->v4, &C->v5, &C->v6, &C->rw.r1,
+                            &C->rv.r1, &C->rt.r1})
+    b->alloc(L);
+  for (EigSlot* e : {&C->ew, &C->ev, &C->et, &C->e1, &C->e2}) {
+    e->P.alloc(L2);
+    e->sig.alloc(L);
+  }
+  C->partial.alloc(std::max(kReduceBlocks, 64));
+  C->scal.alloc(64);
+  C->bounds.alloc(2 + 2 * L);
+  C->iscal.alloc(16);
+}
+
+// Input array -> device pointer (copies host arrays into staging slot k).
+const double* dev_in(kot_ctx* C, int k, const double* p, size_t count) {
+  if (!C->opt.host_pointers) return p;
+  C->stage[k].alloc(count);
+  KOT_CUDA(cudaMemcpyAsync(C->stage[k].p, p, count * sizeof(double), cudaMemcpyHostToDevice, C->st));
+  return C->stage[k].p;
+}
+
+// Copy a device result to the caller's array (device or host).
+void dev_out(kot_ctx* C, double* dst, const double* src, size_t count) {
+  if (!dst) return;
+  KOT_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(double),
+                           C->opt.host_pointers ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                           C->st));
+}
+
+void fetch(kot_ctx* C, int count) {
+  KOT_CUDA(cudaMemcpyAsync(C->hs, C->scal.p, count * sizeof(double), cudaMemcpyDeviceToHost, C->st));
+  KOT_CUDA(cudaStreamSynchronize(C->st));
+}
+
+// ------------------------------------------------------------------ operators (Sec. 4.1)
+// out = Phi*(gamma) = R diag(gamma) R^T
+void phi_star(kot_ctx* C, const double* gamma, double* out) {
+  const int l = C->l;
+  gemm_f64(C->st, false, true, l, l, l, 1.0, C->R.p, l, C->R.p, l, gamma, 0.0, out, l,
+           G_KLO_ROW | G_KLO_COL | G_SYM);
+}
+
+// out = Phi(X)_i = (R^T X R)_ii ; tmp: l x l scratch
+void phi(kot_ctx* C, const double* X, double* out, double* tmp) {
+  const int l = C->l;
+  gemm_f64(C->st, false, false, l, l, l, 1.0, X, l, C->R.p, l, nullptr, 0.0, tmp, l, G_KHI_COL);
+  coldot_upper(C->st, l, C->R.p, tmp, out);
+}
+
+// out = (Q gamma - z)/(2 lambda2) - Phi(X)
+void grad_gamma(kot_ctx* C, const double* gamma, const double* X, double* out, double* vtmp,
+                double* mtmp) {
+  const int l = C->l;
+  const double s = 1.0 / (2.0 * C->lambda2);
+  gemv_f64(C->st, l, s, C->Q.p, gamma, 0.0, out);
+  axpby(C->st, l, 1.0, out, -s, C->z.p, out);
+  phi(C, X, vtmp, mtmp);
+  axpby(C->st, l, 1.0, out, -1.0, vtmp, out);
+}
+
+// Eigen-decompose Z (read only) into slot e (warm-started from `warm` if valid); reads the
+// alpha-bar count back to the host.
+void eig_into(kot_ctx* C, const double* Z, EigSlot& e, const EigSlot* warm) {
+  const int l = C->l;
+  const double* wp = (warm && warm->valid) ? warm->P.p : nullptr;
+  eig_sym_f64(C->st, l, Z, wp, e.P.p, e.sig.p, C->jw, kMaxSweeps, C->hs);
+  count_nonpos(C->st, l, e.sig.p, C->iscal.p);
+  KOT_CUDA(cudaMemcpyAsync(C->hi, C->iscal.p, sizeof(int), cudaMemcpyDeviceToHost, C->st));
+  KOT_CUDA(cudaStreamSynchronize(C->st));
+  e.nb = C->hi[0];
+  e.valid = true;
+}
+
+// out = Pi_{S+}(Z) from slot e (Eq. (4.4)); out may alias Z.
+void form_proj(kot_ctx* C, const double* Z, const EigSlot& e, double* out) {
+  const int l = C->l, nb = e.nb, na = l - nb;
+  if (na == 0) {
+    fill(C->st, (size_t)l * l, 0.0, out);
+  } else if (na <= nb) {
+    const double* Pa = e.P.p + nb;
+    gemm_f64(C->st, false, true, l, l, na, 1.0, Pa, l, Pa, l, e.sig.p + nb, 0.0, out, l, G_SYM);
+  } else {
+    // Pi_{S+}(Z) = Z - P_abar diag(sig_abar) P_abar^T (fewer columns)
+    if (out != Z) copy_mat(C->st, l, l, Z, l, out, l);
+    if (nb > 0)
+      gemm_f64(C->st, false, true, l, l, nb, -1.0, e.P.p, l, e.P.p, l, e.sig.p, 1.0, out, l, G_SYM);
+  }
+}
+
+// M <- Pi_{S+}(M) with slot e (warm-started from itself)
+void proj_inplace(kot_ctx* C, double* M, EigSlot& e) {
+  const int l = C->l;
+  copy_mat(C->st, l, l, M, l, C->M6.p, l);
+  symmetrize(C->st, l, C->M6.p);
+  eig_into(C, C->M6.p, e, &e);
+  form_proj(C, C->M6.p, e, M);
+}
+
+// R(w) of Eq. (4.2) into r; eigen-decomposition of Z(w) into e.
+void residual(kot_ctx* C, const double* gamma, const double* X, EigSlot& e, const EigSlot* warm,
+              ResState& r) {
+  const int l = C->l;
+  const size_t L2 = (size_t)l * l;
+  phi_star(C, gamma, C->M1.p);
+  axpby(C->st, L2, 1.0, X, -1.0, C->M1.p, C->M1.p);          // Z = X - Phi*(gamma)
+  add_diag(C->st, l, -C->lambda1, C->M1.p, l);                // ... - lambda1 I
+  symmetrize(C->st, l, C->M1.p);
+  eig_into(C, C->M1.p, e, warm);
+  form_proj(C, C->M1.p, e, C->M2.p);
+  axpby(C->st, L2, 1.0, X, -1.0, C->M2.p, r.r2.p);            // r2 = X - Pi(Z)
+  grad_gamma(C, gamma, X, r.r1.p, C->v1.p, C->M3.p);           // r1
+  sumsq_f64(C->st, l, r.r1.p, C->scal.p, C->partial.p);
+  sumsq_f64(C->st, L2, r.r2.p, C->scal.p + 1, C->partial.p);
+  fetch(C, 2);
+  r.n1 = std::sqrt(C->hs[0]);
+  r.n2 = std::sqrt(C->hs[1]);
+  r.norm = r.n1 + r.n2;
+  if (!std::isfinite(r.norm)) fail(KOT_ERR_NONFINITE, "residual is not finite");
+}
+
+// out = T_k[S] (Sec. 4.3) with the eigen-decomposition in e and regularisation mu.
+// |alpha| <= |alpha-bar|: G + G^T with U = P_a^T S (8 |alpha| l^2 flops);
+// otherwise the complement form S/mu - P((E/mu - Psi) o (P^T S P))P^T (8 |alpha-bar| l^2).
+void t_apply(kot_ctx* C, const EigSlot& e, double mu, const double* S, double* out) {
+  const int l = C->l, nb = e.nb, na = l - nb;
+  const size_t L2 = (size_t)l * l;
+  if (na == 0) {
+    fill(C->st, L2, 0.0, out);
+    return;
+  }
+  if (nb == 0) {
+    axpby(C->st, L2, 1.0 / mu, S, 0.0, nullptr, out);
+    return;
+  }
+  const bool comp = na > nb;
+  const int rows = comp ? nb : na;
+  const double* Ps = comp ? e.P.p : e.P.p + nb;   // l x rows, ld l
+  gemm_f64(C->st, true, false, rows, l, l, 1.0, Ps, l, S, l, nullptr, 0.0, C->TU.p, l, 0);
+  gemm_f64(C->st, false, false, rows, l, l, 1.0, C->TU.p, l, e.P.p, l, nullptr, 0.0, C->TV.p, l, 0);
+  t_weights(C->st, l, nb, e.sig.p, mu, comp ? 1 : 0, C->TV.p);
+  gemm_f64(C->st, false, true, rows, l, l, 1.0, C->TV.p, l, e.P.p, l, nullptr, 0.0, C->TW.p, l, 0);
+  gemm_f64(C->st, false, false, l, l, rows, 1.0, Ps, l, C->TW.p, l, nullptr, 0.0, C->TG.p, l, 0);
+  sym_sum(C->st, l, C->TG.p, S, 1.0 / mu, comp ? 1 : 0, out);
+}
+
+// Algorithm 1 at w (residual r, eigen-decomposition e).  Returns CG iterations.
+int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu, double cg_tol_abs,
+                     double* dgam, double* dX) {
+  const int l = C->l;
+  const size_t L2 = (size_t)l * l;
+  cudaStream_t st = C->st;
+  double* rT = C->M1.p;     // r2 + T[r2]
+  double* at2 = C->M3.p;    // (a2 + T[a2])/(mu + 1)
+  double* TPx = C->M4.p;    // T[Phi*(x)]
+  double* a1 = C->v2.p;
+  double* ev = C->v3.p;     // CG residual
+  double* pv = C->v4.p;     // CG direction
+  double* Hp = C->v6.p;
+  t_apply(C, e, mu, r.r2.p, rT);
+  axpby(st, L2, 1.0, r.r2.p, 1.0, rT, rT);
+  phi(C, rT, C->v1.p, C->M2.p);
+  axpby(st, l, -1.0, r.r1.p, -1.0 / (mu + 1.0), C->v1.p, a1);
+  axpby(st, L2, -1.0 / (mu + 1.0), rT, 0.0, nullptr, at2);
+  fill(st, l, 0.0, dgam);
+  fill(st, L2, 0.0, TPx);
+  KOT_CUDA(cudaMemcpyAsync(ev, a1, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  KOT_CUDA(cudaMemcpyAsync(pv, a1, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  const int cap = cg_tol_abs > 0 ? 10 * l + 50 : C->opt.cg_max_iter;
+  int it = 0;
+  double ee = 0;
+  while (true) {
+    // stop test at the current iterate: ||e|| vs tau min(1, kappa ||r|| ||dw||)
+    sumsq_f64(st, l, ev, C->scal.p, C->partial.p);
+    sumsq_f64(st, l, dgam, C->scal.p + 1, C->partial.p);
+    axpby(st, L2, 1.0, at2, -1.0, TPx, C->M5.p);
+    sumsq_f64(st, L2, C->M5.p, C->scal.p + 2, C->partial.p);
+    fetch(C, 3);
+    ee = C->hs[0];
+    const double enorm = std::sqrt(ee);
+    if (!std::isfinite(enorm)) fail(KOT_ERR_NONFINITE, "CG residual is not finite");
+    bool stop;
+    if (cg_tol_abs > 0) stop = enorm <= cg_tol_abs;
+    else {
+      const double dw = std::sqrt(C->hs[1]) + std::sqrt(C->hs[2]);
+      stop = enorm <= C->opt.tau * std::min(1.0, C->opt.kappa * r.norm * dw);
+    }
+    if (stop || it >= cap) break;
+    // Hp = Q p/(2 lambda2) + mu p + Phi(T[Phi*(p)])
+    phi_star(C, pv, C->M5.p);
+    t_apply(C, e, mu, C->M5.p, C->M6.p);
+    phi(C, C->M6.p, C->v5.p, C->M5.p);
+    gemv_f64(st, l, 1.0 / (2.0 * C->lambda2), C->Q.p, pv, 0.0, Hp);
+    axpby(st, l, mu, pv, 1.0, Hp, Hp);
+    axpby(st, l, 1.0, Hp, 1.0, C->v5.p, Hp);
+    dot_f64(st, l, pv, Hp, C->scal.p + 3, C->partial.p);
+    KOT_CUDA(cudaMemcpyAsync(C->hs + 3, C->scal.p + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+    KOT_CUDA(cudaStreamSynchronize(st));
+    const double pHp = C->hs[3];
+    if (!(pHp > 0.0)) break;
+    const double a = ee / pHp;
+    axpby(st, l, 1.0, dgam, a, pv, dgam);
+    axpby(st, L2, 1.0, TPx, a, C->M6.p, TPx);
+    axpby(st, l, 1.0, ev, -a, Hp, ev);
+    sumsq_f64(st, l, ev, C->scal.p + 4, C->partial.p);
+    KOT_CUDA(cudaMemcpyAsync(C->hs + 4, C->scal.p + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+    KOT_CUDA(cudaStreamSynchronize(st));
+    const double beta = C->hs[4] / ee;
+    axpby(st, l, 1.0, ev, beta, pv, pv);
+    ++it;
+  }
+  axpby(st, L2, 1.0, at2, -1.0, TPx, dX);
+  return it;
+}
+
+// One projected extragradient step on (vg, vX) with step eta (Korpelevich).
+void eg_step(kot_ctx* C, double eta) {
+  const int l = C->l;
+  const size_t L2 = (size_t)l * l;
+  cudaStream_t st = C->st;
+  // F at v
+  grad_gamma(C, C->vg.p, C->vX.p, C->v2.p, C->v1.p, C->M3.p);    // v2 = F_gamma(v)
+  phi_star(C, C->vg.p, C->M1.p);
+  add_diag(st, l, C->lambda1, C->M1.p, l);                        // M1 = F_X(v)
+  axpby(st, l, 1.0, C->vg.p, -eta, C->v2.p, C->v4.p);             // gamma_h
+  axpby(st, L2, 1.0, C->vX.p, -eta, C->M1.p, C->M2.p);            // X_v - eta F_X(v)
+  proj_inplace(C, C->M2.p, C->e1);                                // X_h
+  // F at h
+  grad_gamma(C, C->v4.p, C->M2.p, C->v3.p, C->v1.p, C->M3.p);
+  phi_star(C, C->v4.p, C->M1.p);
+  add_diag(st, l, C->lambda1, C->M1.p, l);
+  axpby(st, l, 1.0, C->vg.p, -eta, C->v3.p, C->vg.p);
+  axpby(st, L2, 1.0, C->vX.p, -eta, C->M1.p, C->vX.p);
+  proj_inplace(C, C->vX.p, C->e2);
+}
+
+double pair_inner(kot_ctx* C, const ResState& r, const double* dg, const double* dX) {
+  const int l = C->l;
+  dot_f64(C->st, l, r.r1.p, dg, C->scal.p, C->partial.p);
+  dot_f64(C->st, l * l, r.r2.p, dX, C->scal.p + 1, C->partial.p);
+  sumsq_f64(C->st, l, dg, C->scal.p + 2, C->partial.p);
+  sumsq_f64(C->st, (size_t)l * l, dX, C->scal.p + 3, C->partial.p);
+  fetch(C, 4);
+  return C->hs[0] + C->hs[1];
+}
+
+void swap_slots(EigSlot& a, EigSlot& b) {
+  std::swap(a.P, b.P);
+  std::swap(a.sig, b.sig);
+  std::swap(a.nb, b.nb);
+  std::swap(a.valid, b.valid);
+}
+void swap_res(ResState& a, ResState& b) {
+  std::swap(a.r1, b.r1);
+  std::swap(a.r2, b.r2);
+  std::swap(a.n1, b.n1);
+  std::swap(a.n2, b.n2);
+  std::swap(a.norm, b.norm);
+}
+
+double objective_and_ot(kot_ctx* C, const double* gamma, double* ot) {
+  const int l = C->l;
+  gemv_f64(C->st, l, 1.0, C->Q.p, gamma, 0.0, C->v1.p);
+  dot_f64(C->st, l, gamma, C->v1.p, C->scal.p, C->partial.p);
+  dot_f64(C->st, l, gamma, C->z.p, C->scal.p + 1, C->partial.p);
+  axpby(C->st, l, 1.0, C->w_mu.p, 1.0, C->w_nu.p, C->v2.p);
+  dot_f64(C->st, l, gamma, C->v2.p, C->scal.p + 2, C->partial.p);
+  fetch(C, 3);
+  const double l2 = C->lambda2;
+  *ot = C->q2 / (2 * l2) - C->hs[2] / (2 * l2);
+  return C->hs[0] / (4 * l2) - C->hs[1] / (2 * l2) + C->q2 / (4 * l2);
+}
+
+void compute_eg_L(kot_ctx* C) {
+  const int l = C->l;
+  // Kt = R^T R into M1
+  gemm_f64(C->st, true, false, l, l, l, 1.0, C->R.p, l, C->R.p, l, nullptr, 0.0, C->M1.p, l,
+           G_KHI_ROW | G_KHI_COL | G_SYM);
+  rowsum_bounds(C->st, l, C->Q.p, C->M1.p, C->bounds.p);
+  KOT_CUDA(cudaMemcpyAsync(C->hs, C->bounds.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, C->st));
+  KOT_CUDA(cudaStreamSynchronize(C->st));
+  C->eg_L = C->hs[0] / (2 * C->lambda2) + std::sqrt(C->hs[1]);
+}
+
+void factor(kot_ctx* C) {
+  const int l = C->l;
+  k_maxdiag<<<1, 256, 0, C->st>>>(l, C->K.p, C->scal.p);
+  KOT_CHECK_LAUNCH();
+  fetch(C, 1);
+  const double scale = C->hs[0];
+  double rel = C->opt.jitter;
+  while (true) {
+    C->eps = rel * scale;
+    copy_mat(C->st, l, l, C->K.p, l, C->R.p, l);
+    cholesky_upper_f64(C->st, l, C->R.p, C->eps, C->iscal.p);
+    KOT_CUDA(cudaMemcpyAsync(C->hi, C->iscal.p, sizeof(int), cudaMemcpyDeviceToHost, C->st));
+    KOT_CUDA(cudaStreamSynchronize(C->st));
+    if (C->hi[0] == 0) break;
+    rel *= 10.0;
+    if (rel > C->opt.jitter_max * (1 + 1e-12))
+      fail(KOT_ERR_NOT_PD, "K + eps I is not positive definite up to the jitter limit");
+  }
+}
+
+void reset_slots(kot_ctx* C) {
+  for (EigSlot* e : {&C->ew, &C->ev, &C->et, &C->e1, &C->e2}) e->valid = false;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+
+namespace {
+kot_status run(kot_ctx* C, const std::function<void()>& body) {
+  struct Install {
+    explicit Install(kot_ctx* c) { set_current_profiler(c && c->prof.mask ? &c->prof : nullptr); }
+    ~Install() { set_current_profiler(nullptr); }
+  } install(C);
+  try {
+    body();
+    return KOT_OK;
+  } catch (const Error& e) {
+    if (C) C->err = e.what;
+    return e.status;
+  } catch (const std::exception& e) {
+    if (C) C->err = e.what();
+    return KOT_ERR_CUDA;
+  }
+}
+}  // namespace
+
+extern "C" {
+
+kot_status kot_default_options(kot_options* opt) {
+  if (!opt) return KOT_ERR_INVALID;
+  set_defaults(opt);
+  return KOT_OK;
+}
+
+kot_status kot_create(kot_ctx** out, const kot_options* opt) {
+  if (!out) return KOT_ERR_INVALID;
+  *out = nullptr;
+  kot_options o;
+  if (opt) o = *opt;
+  else set_defaults(&o);
+  if (o.max_iter < 0 || o.cg_max_iter < 0 || !(o.tau > 0 && o.tau < 1) || !(o.kappa > 0) ||
+      !(o.alpha1 > 0) || !(o.alpha2 >= o.alpha1) || !(o.beta0 > 0) || !(o.beta1 > 0) ||
+      !(o.beta2 > 0) || !(o.theta0 > 0) || !(o.theta_min > 0) || !(o.theta_max >= o.theta_min) ||
+      !(o.jitter >= 0) || !(o.jitter_max >= o.jitter) ||
+      (o.precision != KOT_FP64 && o.precision != KOT_MIXED))
+    return KOT_ERR_INVALID;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) {
+    cudaGetLastError();
+    return KOT_ERR_CUDA;
+  }
+  kot_ctx* C = new kot_ctx();
+  C->opt = o;
+  kot_status s = run(C, [&] {
+    KOT_CUDA(cudaSetDevice(o.device));
+    if (o.stream) {
+      C->st = (cudaStream_t)o.stream;
+    } else {
+      KOT_CUDA(cudaStreamCreateWithFlags(&C->st, cudaStreamNonBlocking));
+      C->own_stream = true;
+    }
+    KOT_CUDA(cudaMallocHost(&C->hs, 64 * sizeof(double)));
+    KOT_CUDA(cudaMallocHost(&C->hi, 16 * sizeof(int)));
+  });
+  if (s != KOT_OK) {
+    kot_destroy(C);
+    return s;
+  }
+  *out = C;
+  return KOT_OK;
+}
+
+kot_status kot_destroy(kot_ctx* C) {
+  if (!C) return KOT_OK;
+  cudaSetDevice(C->opt.device);
+  if (C->st) cudaStreamSynchronize(C->st);
+  for (DevBuf<double>* b : {&C->Q, &C->K, &C->R, &C->z, &C->w_mu, &C->w_nu, &C->c, &C->g, &C->X,
+                            &C->vg, &C->vX, &C->tg, &C->tX, &C->dg, &C->dX, &C->M1, &C->M2,
+                            &C->M3, &C->M4, &C->M5, &C->M6, &C->TU, &C->TV, &C->TW, &C->TG,
+                            &C->v1, &C->v2, &C->v3, &C->v4, &C->v5, &C->v6, &C->partial,
+                            &C->scal, &C->bounds, &C->rw.r1, &C->rw.r2, &C->rv.r1, &C->rv.r2,
+                            &C->rt.r1, &C->rt.r2, &C->jw.A, &C->jw.V, &C->jw.rot, &C->jw.partial,
+                            &C->jw.scal})
+    b->release();
+  for (auto& b : C->stage) b.release();
+  for (EigSlot* e : {&C->ew, &C->ev, &C->et, &C->e1, &C->e2}) {
+    e->P.release();
+    e->sig.release();
+  }
+  C->iscal.release();
+  C->jw.pairs.release();
+  C->jw.rank.release();
+  if (C->hs) cudaFreeHost(C->hs);
+  if (C->hi) cudaFreeHost(C->hi);
+  C->prof.release();
+  if (C->own_stream && C->st) cudaStreamDestroy(C->st);
+  delete C;
+  return KOT_OK;
+}
+
+const char* kot_last_error(const kot_ctx* C) { return C ? C->err.c_str() : "null context"; }
+
+kot_status kot_build_features(kot_ctx* C, int d, int n, const double* X, const double* Y, int l,
+                              const double* Xf, const double* Yf, double sigma, double lambda1,
+                              double lambda2) {
+  if (!C) return KOT_ERR_INVALID;
+  if (d < 1 || n < 1 || l < 1 || d > 65536 || l > 32768 || !X || !Y || !Xf || !Yf ||
+      !pos_finite(sigma) || !pos_finite(lambda1) || !pos_finite(lambda2)) {
+    C->err = "kot_build_features: invalid argument";
+    return KOT_ERR_INVALID;
+  }
+  return run(C, [&] {
+    KOT_CUDA(cudaSetDevice(C->opt.device));
+    C->have = false;
+    C->l = l;
+    ensure(C, l);
+    reset_slots(C);
+    cudaStream_t st = C->st;
+    const double* dX = dev_in(C, 0, X, (size_t)n * d);
+    const double* dY = dev_in(C, 1, Y, (size_t)n * d);
+    const double* dXf = dev_in(C, 2, Xf, (size_t)l * d);
+    const double* dYf = dev_in(C, 3, Yf, (size_t)l * d);
+    const double inv2s2 = 1.0 / (2.0 * sigma * sigma);
+    embed_f64(st, n, d, l, dX, dXf, inv2s2, C->w_mu.p);
+    embed_f64(st, n, d, l, dY, dYf, inv2s2, C->w_nu.p);
+    const int pb = pair_blocks(n);
+    C->stage[7].alloc(pb);
+    pair_mean_f64(st, n, d, dX, inv2s2, C->scal.p + 10, C->stage[7].p, pb);
+    pair_mean_f64(st, n, d, dY, inv2s2, C->scal.p + 11, C->stage[7].p, pb);
+    gram_f64(st, l, d, dXf, dYf, inv2s2, lambda2, C->w_mu.p, C->w_nu.p, C->Q.p, C->K.p, C->c.p, C->z.p);
+    KOT_CUDA(cudaMemcpyAsync(C->hs + 10, C->scal.p + 10, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    KOT_CUDA(cudaStreamSynchronize(st));
+    C->q2 = C->hs[10] + C->hs[11];
+    C->lambda1 = lambda1;
+    C->lambda2 = lambda2;
+    factor(C);
+    compute_eg_L(C);
+    C->have = true;
+  });
+}
+
+kot_status kot_set_features(kot_ctx* C, int l, const double* Q, const double* z, double q2,
+                            const double* R, double lambda1, double lambda2) {
+  if (!C) return KOT_ERR_INVALID;
+  if (l < 1 || l > 32768 || !Q || !z || !R || !std::isfinite(q2) || !pos_finite(lambda1) ||
+      !pos_finite(lambda2)) {
+    C->err = "kot_set_features: invalid argument";
+    return KOT_ERR_INVALID;
+  }
+  return run(C, [&] {
+    KOT_CUDA(cudaSetDevice(C->opt.device));
+    C->have = false;
+    C->l = l;
+    ensure(C, l);
+    reset_slots(C);
+    const size_t L2 = (size_t)l * l;
+    const double* dQ = dev_in(C, 0, Q, L2);
+    const double* dz = dev_in(C, 1, z, l);
+    const double* dR = dev_in(C, 2, R, L2);
+    copy_mat(C->st, l, l, dQ, l, C->Q.p, l);
+    KOT_CUDA(cudaMemcpyAsync(C->z.p, dz, l * sizeof(double), cudaMemcpyDeviceToDevice, C->st));
+    KOT_CUDA(cudaMemcpyAsync(C->w_mu.p, dz, l * sizeof(double), cudaMemcpyDeviceToDevice, C->st));
+    fill(C->st, l, 0.0, C->w_nu.p);
+    fill(C->st, l, 0.0, C->c.p);
+    copy_mat(C->st, l, l, dR, l, C->R.p, l);
+    zero_lower(C->st, l, C->R.p);                        // rows below the diagonal ignored
+    gemm_f64(C->st, true, false, l, l, l, 1.0, C->R.p, l, C->R.p, l, nullptr, 0.0, C->K.p, l,
+             G_KHI_ROW | G_KHI_COL | G_SYM);             // K = R^T R
+    C->q2 = q2;
+    C->lambda1 = lambda1;
+    C->lambda2 = lambda2;
+    C->eps = 0.0;
+    compute_eg_L(C);
+    C->have = true;
+  });
+}
+
+kot_status kot_get_features(kot_ctx* C, double* Q, double* K, double* R, double* z, double* w_mu,
+                            double* w_nu, double* c, double* q2, double* eps) {
+  if (!C) return KOT_ERR_INVALID;
+  if (!C->have) {
+    C->err = "kot_get_features: no features";
+    return KOT_ERR_STATE;
+  }
+  return run(C, [&] {
+    KOT_CUDA(cudaSetDevice(C->opt.device));
+    const int l = C->l;
+    const size_t L2 = (size_t)l * l;
+    dev_out(C, Q, C->Q.p, L2);
+    dev_out(C, K, C->K.p, L2);
+    dev_out(C, R, C->R.p, L2);
+    dev_out(C, z, C->z.p, l);
+    dev_out(C, w_mu, C->w_mu.p, l);
+    dev_out(C, w_nu, C->w_nu.p, l);
+    dev_out(C, c, C->c.p, l);
+    C->hs[0] = C->q2;
+    C->hs[1] = C->eps;
+    if (q2) KOT_CUDA(cudaMemcpyAsync(q2, C->hs, sizeof(double), cudaMemcpyDefault, C->st));
+    if (eps) KOT_CUDA(cudaMemcpyAsync(eps, C->hs + 1, sizeof(double), cudaMemcpyDefault, C->st));
+    KOT_CUDA(cudaStreamSynchronize(C->st));
+  });
+}
+
+kot_status kot_residual(kot_ctx* C, const double* gamma, const double* X, double* r1, double* r2,
+                        double* proj, double* sig, double* norms) {
+  if (!C) return KOT_ERR_INVALID;
+  if (!gamma || !X) {
+    C->err = "kot_residual: gamma and X are required";
+    return KOT_ERR_INVALID;
+  }
+  if (!C->have) {
+    C->err = "kot_residual: no features";
+    return KOT_ERR_STATE;
+  }
+  return run(C, [&] {
+    KOT_CUDA(cudaSetDevice(C->opt.device));
+    const int l = C->l;
+    const size_t L2 = (size_t)l * l;
+    const double* dg = dev_in(C, 0, gamma, l);
+    const double* dXm = dev_in(C, 1, X, L2);
+    residual(C, dg, dXm, C->ew, nullptr, C->rw);
+    dev_out(C, r1, C->rw.r1.p, l);
+    dev_out(C, r2, C->rw.r2.p, L2);
+    dev_out(C, proj, C->M2.p, L2);
+    dev_out(C, sig, C->ew.sig.p, l);
+    if (norms) {
+      double h[3] = {C->rw.n1, C->rw.n2, C->rw.norm};
+      KOT_CUDA(cudaMemcpyAsync(norms, h, sizeof(h), cudaMemcpyDefault, C->st));
+    }
+    KOT_CUDA(cudaStreamSynchronize(C->st));
+  });
+}
+
+kot_status kot_newton_direction(kot_ctx* C, const double* gamma, const double* X, double mu,
+                                double cg_tol_abs, double* dgamma, double* dX, int* cg_iters) {
+  if (!C) return KOT_ERR_INVALID;
+  if (!gamma || !X || !dgamma || !dX || !pos_finite(mu) || !std::isfinite(cg_tol_abs)) {
+    C->err = "kot_newton_direction: invalid argument";
+    return KOT_ERR_INVALID;
+  }
+  if (!C->have) {
+    C->err = "kot_newton_direction: no features";
+    return KOT_ERR_STATE;
+  }
+  return run(C, [&] {
+    KOT_CUDA(cudaSetDevice(C->opt.device));
+    const int l = C->l;
+    const size_t L2 = (size_t)l * l;
+    const double* dg = dev_in(C, 0, gamma, l);
+    const double* dXm = dev_in(C, 1, X, L2);
+    residual(C, dg, dXm, C->ew, nullptr, C->rw);
+    const int it = newton_direction(C, C->rw, C->ew, mu, cg_tol_abs, C->dg.p, C->dX.p);
+    dev_out(C, dgamma, C->dg.p, l);
+    dev_out(C, dX, C->dX.p, L2);
+    KOT_CUDA(cudaStreamSynchronize(C->st));
+    if (cg_iters) *cg_iters = it;
+  });
+}
+
+kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_out,
+                         const double* gamma0, const double* X0, kot_result* res) {
+  if (!C) return KOT_ERR_INVALID;
+  if (!gamma_out || !pos_finite(tol)) {
+    C->err = "kot_ssn_solve: invalid argument";
+    return KOT_ERR_INVALID;
+  }
+  if (!C->have) {
+    C->err = "kot_ssn_solve: no features";
+    return KOT_ERR_STATE;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  kot_result R{};
+  bool converged = false;
+  kot_status s = run(C, [&] {
+    KOT_CUDA(cudaSetDevice(C->opt.device));
+    const int l = C->l;
+    const size_t L2 = (size_t)l * l;
+    cudaStream_t st = C->st;
+    const kot_options& o = C->opt;
+    reset_slots(C);
+    if (gamma0) {
+      const double* p = dev_in(C, 0, gamma0, l);
+      KOT_CUDA(cudaMemcpyAsync(C->g.p, p, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+      fill(st, l, 0.0, C->g.p);
+    }
+    if (X0) {
+      const double* p = dev_in(C, 1, X0, L2);
+      KOT_CUDA(cudaMemcpyAsync(C->X.p, p, L2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+      fill(st, L2, 0.0, C->X.p);
+    }
+    KOT_CUDA(cudaMemcpyAsync(C->vg.p, C->g.p, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    KOT_CUDA(cudaMemcpyAsync(C->vX.p, C->X.p, L2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    double theta = o.theta0;
+    const double eta = o.eg_step > 0 ? o.eg_step : 1.0 / C->eg_L;
+    residual(C, C->g.p, C->X.p, C->ew, nullptr, C->rw);
+    C->hist.clear();
+    if (o.record_history) C->hist.push_back(C->rw.norm);
+    int it = 0, acc = 0, egt = 0, cgt = 0;
+    while (C->rw.norm > tol && it < o.max_iter) {
+      if (o.use_eg) {
+        eg_step(C, eta);
+        residual(C, C->vg.p, C->vX.p, C->ev, &C->ev, C->rv);
+      }
+      const double mu = theta * C->rw.norm;
+      cgt += newton_direction(C, C->rw, C->ew, mu, 0.0, C->dg.p, C->dX.p);
+      axpby(st, l, 1.0, C->g.p, 1.0, C->dg.p, C->tg.p);
+      axpby(st, L2, 1.0, C->X.p, 1.0, C->dX.p, C->tX.p);
+      residual(C, C->tg.p, C->tX.p, C->et, &C->ew, C->rt);
+      const double inner = pair_inner(C, C->rt, C->dg.p, C->dX.p);
+      const double dwn = std::sqrt(C->hs[2]) + std::sqrt(C->hs[3]);
+      const double rho = -inner;
+      if (rho >= o.alpha2 * dwn * dwn) theta = std::max(o.theta_min, o.beta0 * theta);
+      else if (rho >= o.alpha1 * dwn * dwn) theta = o.beta1 * theta;
+      else theta = std::min(o.theta_max, o.beta2 * theta);
+      if (!o.use_eg || C->rt.norm <= C->rv.norm) {
+        std::swap(C->g, C->tg);
+        std::swap(C->X, C->tX);
+        swap_res(C->rw, C->rt);
+        swap_slots(C->ew, C->et);
+        ++acc;
+      } else {
+        KOT_CUDA(cudaMemcpyAsync(C->g.p, C->vg.p, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        KOT_CUDA(cudaMemcpyAsync(C->X.p, C->vX.p, L2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        swap_res(C->rw, C->rv);
+        swap_slots(C->ew, C->ev);
+        // the EG sequence keeps its own basis: copy it back for the next R(v) warm start
+        KOT_CUDA(cudaMemcpyAsync(C->ev.P.p, C->ew.P.p, L2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        KOT_CUDA(cudaMemcpyAsync(C->ev.sig.p, C->ew.sig.p, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        C->ev.nb = C->ew.nb;
+        C->ev.valid = true;
+        ++egt;
+      }
+      ++it;
+      if (o.record_history) C->hist.push_back(C->rw.norm);
+    }
+    converged = C->rw.norm <= tol;
+    double ot = 0;
+    const double obj = objective_and_ot(C, C->g.p, &ot);
+    dev_out(C, gamma_out, C->g.p, l);
+    dev_out(C, X_out, C->X.p, L2);
+    KOT_CUDA(cudaStreamSynchronize(st));
+    R.iters = it;
+    R.ssn_accepted = acc;
+    R.eg_taken = egt;
+    R.cg_total = cgt;
+    R.residual = C->rw.norm;
+    R.r1_norm = C->rw.n1;
+    R.r2_norm = C->rw.n2;
+    R.objective = obj;
+    R.ot_hat = ot;
+    R.eps = C->eps;
+  });
+  if (s == KOT_OK && !converged) {
+    s = KOT_ERR_NO_CONVERGENCE;
+    C->err = "kot_ssn_solve: iteration cap reached";
+  }
+  R.status = s;
+  R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (res) *res = R;
+  return s;
+}
+
+kot_status kot_launch_count(long long* out) {
+  if (!out) return KOT_ERR_INVALID;
+  *out = launch_total();
+  return KOT_OK;
+}
+
+kot_status kot_profile(kot_ctx* C, int mask) {
+  if (!C || mask < 0) return KOT_ERR_INVALID;
+  return run(C, [&] {
+    KOT_CUDA(cudaSetDevice(C->opt.device));
+    C->prof.reset();
+    C->prof.mask = mask;
+  });
+}
+
+kot_status kot_profile_read(kot_ctx* C, int cls, kot_kernel_stats* out) {
+  if (!C || !out || cls < 0 || cls >= KC_COUNT) return KOT_ERR_INVALID;
+  return run(C, [&] {
+    C->prof.collect();
+    out->launches = C->prof.launches[cls];
+    out->ms = C->prof.ms[cls];
+    out->flops = C->prof.flops[cls];
+    out->bytes = C->prof.bytes[cls];
+  });
+}
+
+kot_status kot_get_history(kot_ctx* C, double* hist, int cap, int* count) {
+  if (!C || !hist || cap < 0 || !count) return KOT_ERR_INVALID;
+  const int m = std::min<int>(cap, (int)C->hist.size());
+  std::copy(C->hist.begin(), C->hist.begin() + m, hist);
+  *count = m;
+  return KOT_OK;
+}
+
+kot_status kot_batch_solve(kot_ctx* C, int B, const kot_problem* probs, kot_result* res) {
+  if (!C) return KOT_ERR_INVALID;
+  if (B < 0 || (B > 0 && (!probs || !res))) {
+    C->err = "kot_batch_solve: invalid argument";
+    return KOT_ERR_INVALID;
+  }
+  for (int i = 0; i < B; ++i) {
+    const kot_problem& p = probs[i];
+    if (p.d < 1 || p.n < 1 || p.l < 1 || !p.X || !p.Y || !p.Xf || !p.Yf || !p.gamma_out ||
+        !pos_finite(p.sigma) || !pos_finite(p.lambda1) || !pos_finite(p.lambda2) ||
+        !pos_finite(p.tol)) {
+      C->err = "kot_batch_solve: invalid problem " + std::to_string(i);
+      return KOT_ERR_INVALID;
+    }
+  }
+  // largest problems first (cost grows like l^3)
+  std::vector<int> order(B);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return probs[a].l > probs[b].l; });
+  kot_status first = KOT_OK;
+  for (int i : order) {
+    const kot_problem& p = probs[i];
+    kot_status s = kot_build_features(C, p.d, p.n, p.X, p.Y, p.l, p.Xf, p.Yf, p.sigma, p.lambda1,
+                                      p.lambda2);
+    if (s == KOT_OK) s = kot_ssn_solve(C, p.tol, p.gamma_out, nullptr, nullptr, nullptr, &res[i]);
+    else {
+      res[i] = kot_result{};
+      res[i].status = s;
+    }
+    if (s != KOT_OK && first == KOT_OK) first = s;
+  }
+  return first;
+}
+
+}  // extern "C"

@@ -1,0 +1,191 @@
+// Internal declarations shared by the CUDA translation units of libkot.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/kot.h"
+
+namespace kot {
+
+// ------------------------------------------------------------------ error plumbing
+struct Error {
+  kot_status status;
+  std::string what;
+};
+
+#define KOT_CUDA(call)                                                                    \
+  do {                                                                                    \
+    cudaError_t e__ = (call);                                                             \
+    if (e__ != cudaSuccess)                                                               \
+      throw ::kot::Error{e__ == cudaErrorMemoryAllocation ? KOT_ERR_OOM : KOT_ERR_CUDA,    \
+                         std::string(#call) + ": " + cudaGetErrorString(e__)};            \
+  } while (0)
+
+// Every kernel launch site is followed by KOT_LAUNCHED(k) with the number of kernels it just
+// launched; the running total is readable through kot_launch_count().
+void note_launches(long long k);
+long long launch_total();
+#define KOT_LAUNCHED(k)                   \
+  do {                                    \
+    ::kot::note_launches(k);              \
+    KOT_CUDA(cudaPeekAtLastError());      \
+  } while (0)
+#define KOT_CHECK_LAUNCH() KOT_LAUNCHED(1)
+
+// ------------------------------------------------------------------ launch profiler
+// Kernel classes the profiler can time (kot_kernel_class in kot.h uses the same numbering).
+enum KClass : int {
+  KC_GEMM_F64 = 0,      // k_gemm_f64
+  KC_JACOBI_ROTATE = 1, // k_rotate (one Jacobi round)
+  KC_JACOBI_ANGLES = 2, // k_angles
+  KC_EMBED = 3,         // k_embed
+  KC_PAIRS = 4,         // k_pair_tiles
+  KC_GRAM = 5,          // k_gram
+  KC_CHOL = 6,          // Cholesky diagonal / panel kernels
+  KC_COUNT = 7
+};
+
+// When a profiler is installed for the calling thread, instrumented launch sites record a CUDA
+// event pair around each launch of an enabled class together with the launch's algorithmic
+// flop and byte counts; collect() waits for the events and accumulates per class.
+struct Profiler {
+  int mask = 0;
+  struct Pending { int cls; cudaEvent_t a, b; double flops, bytes; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  long launches[KC_COUNT] = {};
+  double ms[KC_COUNT] = {}, flops[KC_COUNT] = {}, bytes[KC_COUNT] = {};
+  bool on(int cls) const { return (mask >> cls) & 1; }
+  cudaEvent_t get_event();
+  void begin(cudaStream_t st, int cls, cudaEvent_t* a);
+  void end(cudaStream_t st, int cls, cudaEvent_t a, double fl, double by);
+  void collect();
+  void reset();
+  void release();
+};
+Profiler* current_profiler();
+void set_current_profiler(Profiler* p);
+
+// RAII helper around one launch: `ProfScope ps(st, KC_x, flops, bytes); launch...;`
+struct ProfScope {
+  Profiler* p;
+  cudaStream_t st;
+  int cls;
+  double fl, by;
+  cudaEvent_t a = nullptr;
+  ProfScope(cudaStream_t s, int c, double f, double b) : p(current_profiler()), st(s), cls(c), fl(f), by(b) {
+    if (p && p->on(cls)) p->begin(st, cls, &a);
+    else p = nullptr;
+  }
+  ~ProfScope() {
+    if (p) p->end(st, cls, a, fl, by);
+  }
+};
+
+// ------------------------------------------------------------------ device buffers
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  void alloc(size_t count) {
+    if (count <= n) return;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    KOT_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    n = count;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+// ------------------------------------------------------------------ dense kernels (dense.cu)
+// GEMM flags: which operand is triangular, so the k-range of a tile can be cut.
+enum GemmFlags : int {
+  G_KLO_ROW = 1,   // opA(A)[m,k] == 0 for k < m   (opA(A) upper triangular)
+  G_KLO_COL = 2,   // opB(B)[k,n] == 0 for k < n   (opB(B) lower triangular)
+  G_KHI_COL = 4,   // opB(B)[k,n] == 0 for k > n   (opB(B) upper triangular)
+  G_KHI_ROW = 8,   // opA(A)[m,k] == 0 for k > m   (opA(A) lower triangular)
+  G_SYM = 16       // result is symmetric: compute tiles with n0 >= m0, mirror the rest
+};
+
+// C[M,N] = alpha * sum_k opA(A)[m,k] * s[k] * opB(B)[k,n] + beta * C
+//   opA(A) = A (M x K, lda) or A^T (A stored K x M, lda) ; same for B (K x N or N x K).
+void gemm_f64(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alpha,
+              const double* A, int lda, const double* B, int ldb, const double* s, double beta,
+              double* C, int ldc, int flags);
+
+// out[i] = sum_a R[a,i] * Y[a,i] for a <= i  (Phi(X) = diag(R^T X R) with Y = X R)
+void coldot_upper(cudaStream_t st, int l, const double* R, const double* Y, double* out);
+
+// y = alpha * A x + beta * y (A: n x n row-major)
+void gemv_f64(cudaStream_t st, int n, double alpha, const double* A, const double* x,
+              double beta, double* y);
+
+// Deterministic reductions.  Results land in device memory (one double).
+void dot_f64(cudaStream_t st, int n, const double* x, const double* y, double* out,
+             double* partial);
+// out = sum x^2 over a n-element array
+void sumsq_f64(cudaStream_t st, size_t n, const double* x, double* out, double* partial);
+constexpr int kReduceBlocks = 128;   // size of the partial buffer the reductions need
+
+// Elementwise helpers.
+void axpby(cudaStream_t st, size_t n, double a, const double* x, double b, const double* y,
+           double* out);                                           // out = a x + b y
+void fill(cudaStream_t st, size_t n, double v, double* out);
+void symmetrize(cudaStream_t st, int l, double* A);                // A = (A + A^T)/2
+void add_diag(cudaStream_t st, int l, double v, double* A, int lda);
+void copy_mat(cudaStream_t st, int rows, int cols, const double* A, int lda, double* B, int ldb);
+// out = G + G^T (sign = +1) or S/mu - (G + G^T) (sign = -1, S given)
+void sym_sum(cudaStream_t st, int l, const double* G, const double* S, double inv_mu,
+             int complement, double* out);
+
+// ------------------------------------------------------------------ features (features.cu)
+void embed_f64(cudaStream_t st, int n, int d, int l, const double* S, const double* P,
+               double inv2s2, double* w);                          // w_i = mean_j k(s_j, p_i)
+// sum_ij k(s_i, s_j) / n^2 into *out (partial: kPairBlocks doubles)
+void pair_mean_f64(cudaStream_t st, int n, int d, const double* S, double inv2s2, double* out,
+                   double* partial, int partial_cap);
+int pair_blocks(int n);                                            // partials the above needs
+void gram_f64(cudaStream_t st, int l, int d, const double* Xf, const double* Yf, double inv2s2,
+              double lambda2, const double* w_mu, const double* w_nu, double* Q, double* K,
+              double* c, double* z);
+// Upper Cholesky of A + eps I in place (A: l x l, only the upper triangle is read).  The lower
+// triangle is zeroed.  *info (device int) = 0 on success, j+1 if pivot j was not positive.
+void zero_lower(cudaStream_t st, int l, double* A);        // A[i][j] = 0 for j < i
+void cholesky_upper_f64(cudaStream_t st, int l, double* A, double eps, int* info);
+// bound for the EG step (see kot_options.eg_step): out[0] = max rowsum |Q|, out[1] = max rowsum
+// of (R^T R)_ij^2 given Kt = R^T R.
+void rowsum_bounds(cudaStream_t st, int l, const double* Q, const double* Kt, double* out2);
+
+// ------------------------------------------------------------------ eigen (eig.cu)
+struct JacobiWork {
+  DevBuf<double> A, V;      // lp x lp
+  DevBuf<double> rot;       // lp/2 pairs * 2 (c, s)
+  DevBuf<int> pairs;        // lp
+  DevBuf<int> rank;         // l
+  DevBuf<double> partial, scal;
+};
+
+// Symmetric eigen-decomposition Z = P diag(sig) P^T, sig ascending.  Z: l x l (full
+// symmetric, read only).  If warm != nullptr its columns (an orthogonal l x l basis, row-major)
+// are used as the starting basis.  P: l x l output (row-major, column j = eigenvector j).
+// Returns the number of sweeps taken; throws on non-convergence within max_sweeps.
+int eig_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, double* P,
+                double* sig, JacobiWork& w, int max_sweeps, double* host_scal);
+
+// ------------------------------------------------------------------ Newton pieces (newton.cu)
+// Scale rows of V (na x l) for the G + G^T form of T: columns in alpha by 1/(2 mu), columns in
+// alpha-bar by xi (or the complement weights).  See t_apply in kot_api.cu.
+void t_weights(cudaStream_t st, int l, int nb, const double* sig, double mu, int complement,
+               double* V);
+// Count of eigenvalues <= 0 in sorted sig (device) -> *nb (device int)
+void count_nonpos(cudaStream_t st, int l, const double* sig, int* nb);
+
+}  // namespace kot

@@ -1,0 +1,64 @@
+// Pieces of the Newton direction (Algorithm 1): the weights of the operator T_k (Sec. 4.3) in
+// the cost-reduced G + G^T form and in the complement form, and the alpha / alpha-bar split.
+#include "kot_internal.cuh"
+
+namespace kot {
+
+namespace {
+
+inline int cdiv(size_t a, int b) { return (int)((a + b - 1) / b); }
+
+// xi_ij = eta_ij / (mu + 1 - eta_ij), eta_ij = sig_i / (sig_i - sig_j), i in alpha, j in alpha-bar
+__device__ __forceinline__ double xi_of(double si, double sj, double mu) {
+  const double eta = si / (si - sj);
+  return eta / (mu + 1.0 - eta);
+}
+
+// V: rows x l.  G + G^T form (complement = 0): row r is eigen-index nb + r (in alpha); column j in
+// alpha (j >= nb) is scaled by 1/(2 mu), column j in alpha-bar by xi(sig_{nb+r}, sig_j).
+// Complement form (complement = 1): row r is eigen-index r (in alpha-bar); column j in alpha-bar
+// is scaled by 1/(2 mu), column j in alpha by 1/mu - xi(sig_j, sig_r).
+__global__ void k_t_weights(int rows, int l, int nb, const double* __restrict__ sig, double mu,
+                            int complement, double* __restrict__ V) {
+  const int j = blockIdx.x * 32 + threadIdx.x, r = blockIdx.y * 8 + threadIdx.y;
+  if (r >= rows || j >= l) return;
+  double w;
+  if (!complement) {
+    const int i = nb + r;
+    w = (j >= nb) ? 0.5 / mu : xi_of(sig[i], sig[j], mu);
+  } else {
+    const int i = r;
+    w = (j < nb) ? 0.5 / mu : (1.0 / mu - xi_of(sig[j], sig[i], mu));
+  }
+  V[(size_t)r * l + j] *= w;
+}
+
+__global__ void k_count_nonpos(int l, const double* __restrict__ sig, int* __restrict__ nb) {
+  __shared__ int sh[256];
+  int c = 0;
+  for (int i = threadIdx.x; i < l; i += 256) c += (sig[i] <= 0.0);
+  sh[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *nb = sh[0];
+}
+
+}  // namespace
+
+void t_weights(cudaStream_t st, int l, int nb, const double* sig, double mu, int complement,
+               double* V) {
+  const int rows = complement ? nb : l - nb;
+  if (rows <= 0) return;
+  k_t_weights<<<dim3(cdiv(l, 32), cdiv(rows, 8)), dim3(32, 8), 0, st>>>(rows, l, nb, sig, mu, complement, V);
+  KOT_CHECK_LAUNCH();
+}
+
+void count_nonpos(cudaStream_t st, int l, const double* sig, int* nb) {
+  k_count_nonpos<<<1, 256, 0, st>>>(l, sig, nb);
+  KOT_CHECK_LAUNCH();
+}
+
+}  // namespace kot
