@@ -129,7 +129,7 @@ def cholesky_upper_jittered(K: np.ndarray, jitter: float, jitter_max: float):
             return L.T.copy(), eps
         except np.linalg.LinAlgError:
             rel *= 10.0
-            if rel > jitter_max * (1 + 1e-12):
+            if not rel > 0.0 or rel > jitter_max * (1 + 1e-12):
                 raise
 
 
@@ -288,6 +288,7 @@ class Direction:
     dX: np.ndarray
     cg_iters: int
     cg_res: float
+    stop_margin: float = math.inf   # min over CG stop tests of | ||e|| - threshold | / threshold
 
 
 def newton_direction(F: Features, res: Residual, mu: float, opt: Options,
@@ -326,12 +327,17 @@ def newton_direction(F: Features, res: Residual, mu: float, opt: Options,
     ee = float(e @ e)
     it = 0
 
+    margin = [math.inf]
+
     def stop(x, TPx, ee):
         enorm = math.sqrt(ee)
         if cg_tol_abs is not None:
             return enorm <= cg_tol_abs
         dw = pair_norm(x, at2 - TPx)
-        return enorm <= opt.tau * min(1.0, opt.kappa * rnorm * dw)
+        thr = opt.tau * min(1.0, opt.kappa * rnorm * dw)
+        if thr > 0:
+            margin[0] = min(margin[0], abs(enorm - thr) / thr)
+        return enorm <= thr
 
     while not stop(x, TPx, ee) and it < (opt.cg_max_iter if cg_tol_abs is None else 10 * x.size + 50):
         Hp, TPp = schur_matvec(p)
@@ -346,7 +352,8 @@ def newton_direction(F: Features, res: Residual, mu: float, opt: Options,
         p = e + (ee_new / ee) * p
         ee = ee_new
         it += 1
-    return Direction(dgamma=x, dX=at2 - TPx, cg_iters=it, cg_res=math.sqrt(ee))
+    return Direction(dgamma=x, dX=at2 - TPx, cg_iters=it, cg_res=math.sqrt(ee),
+                     stop_margin=margin[0])
 
 
 # ----------------------------------------------------------------------------------------
@@ -423,12 +430,19 @@ def ssn_solve(F: Features, tol: float, opt: Options | None = None,
             vg, vX = eg_step(F, vg, vX, eta)
             res_v = residual(F, vg, vX)
         mu = theta * res.norm
+        # relative distance of Z(w_k)'s spectrum from 0: how far the alpha split used by this
+        # step is from a rounding-level sign decision (recorded for the parity tests)
+        sig = res.eig.sig
+        split_margin = float(np.min(np.abs(sig)) / max(np.max(np.abs(sig)), 1e-300))
         dirn = newton_direction(F, res, mu, opt)
         cg_tot += dirn.cg_iters
         tg, tX = gamma + dirn.dgamma, X + dirn.dX
         res_t = residual(F, tg, tX)
         dwn = pair_norm(dirn.dgamma, dirn.dX)
         rho = -pair_inner(res_t.r1, res_t.r2, dirn.dgamma, dirn.dX)
+        ratio = rho / (dwn * dwn) if dwn > 0 else math.inf
+        theta_margin = min(abs(ratio - opt.alpha1) / opt.alpha1, abs(ratio - opt.alpha2) / opt.alpha2)
+        accept_margin = (abs(res_t.norm - res_v.norm) / res_v.norm) if opt.use_eg else math.inf
         if rho >= opt.alpha2 * dwn * dwn:
             theta = max(opt.theta_min, opt.beta0 * theta)
         elif rho >= opt.alpha1 * dwn * dwn:
@@ -443,7 +457,10 @@ def ssn_solve(F: Features, tol: float, opt: Options | None = None,
             eg_tk += 1
         it += 1
         if opt.record_history:
-            hist.append((res.norm, mu, dirn.cg_iters, theta))
+            # (||R(w_{k+1})||, mu_k, CG steps, theta_{k+1}, relative margins of the decisions
+            #  taken in iteration k: alpha split, CG stop tests, theta rule, acceptance)
+            hist.append((res.norm, mu, dirn.cg_iters, theta, split_margin, dirn.stop_margin,
+                         theta_margin, accept_margin))
     return Result(gamma=gamma, X=X, residual=res.norm, r1_norm=float(np.linalg.norm(res.r1)),
                   r2_norm=float(np.linalg.norm(res.r2)), objective=objective(F, gamma),
                   ot_hat=ot_estimate(F, gamma), iters=it, ssn_accepted=ssn_acc, eg_taken=eg_tk,

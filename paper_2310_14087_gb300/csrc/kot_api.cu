@@ -406,7 +406,7 @@ void factor(kot_ctx* C) {
     KOT_CUDA(cudaStreamSynchronize(C->st));
     if (C->hi[0] == 0) break;
     rel *= 10.0;
-    if (rel > C->opt.jitter_max * (1 + 1e-12))
+    if (!(rel > 0.0) || rel > C->opt.jitter_max * (1 + 1e-12))
       fail(KOT_ERR_NOT_PD, "K + eps I is not positive definite up to the jitter limit");
   }
 }
