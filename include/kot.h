@@ -36,7 +36,8 @@ typedef enum {
   KOT_ERR_NO_CONVERGENCE = 5, /* iteration cap reached; outputs hold the last iterate    */
   KOT_ERR_NONFINITE = 6,      /* NaN/Inf met in the iteration                            */
   KOT_ERR_TIMEOUT = 7,        /* a bounded device wait gave up                           */
-  KOT_ERR_STATE = 8           /* call order: e.g. solve before features                  */
+  KOT_ERR_STATE = 8,          /* call order: e.g. solve before features                  */
+  KOT_ERR_TOO_LARGE = 9       /* size above the fixed capacity of an allocation-free call */
 } kot_status;
 
 typedef enum {
@@ -173,6 +174,27 @@ kot_status kot_profile(kot_ctx* ctx, int mask);
 /* Total number of kernels this library has launched in the process so far (all contexts). */
 kot_status kot_launch_count(long long* out);
 kot_status kot_profile_read(kot_ctx* ctx, int cls, kot_kernel_stats* out);
+
+/* ---- allocation-free entry point (the paper has no counterpart; an interface addition) ----
+ * ||w||^2 = (1/n^2) sum_{i,j} exp(-||s_i - s_j||^2 / (2 sigma^2)) over the n x d samples S (one
+ * half of q2 in kot_build_features), for callers that must not allocate device memory while
+ * they run: code inside a custom device-memory allocator or pool, a process that reserved all
+ * of its device memory up front, or a host that forbids driver allocations after start-up.
+ * It calls no cudaMalloc/cudaFree and no allocating library routine.  Its per-tile partial sums
+ * live in a fixed device array compiled into the library (32 KB, 4096 doubles, held on every
+ * GPU that loads the library until process exit), which caps n at 4096 samples: larger n
+ * returns KOT_ERR_TOO_LARGE before any GPU work.
+ * S and out (one double) are device pointers on the caller's current device; stream is a
+ * cudaStream_t of that device (NULL = legacy default stream).  The call returns after the
+ * stream has finished (the result is in *out).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the one array and it keeps the last call's partial sums;
+ * every slot a call reads is written by that same call, so nothing needs clearing, but calls
+ * whose GPU work overlaps (other host threads or streams at the same time) race on it and must
+ * be serialised by the caller.  Errors: KOT_ERR_INVALID for n, d < 1, NULL pointers or
+ * sigma <= 0; KOT_ERR_CUDA for a failed CUDA call. */
+kot_status kot_embedding_sqnorm_noalloc(int n, int d, const double* S, double sigma, double* out,
+                                        void* stream);
 
 #ifdef __cplusplus
 }

@@ -19,9 +19,9 @@ LIB_PATH = os.path.join(_PKG, "libkot.so")
 
 # kot_status
 OK, ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_NOT_PD, ERR_NO_CONVERGENCE, ERR_NONFINITE, \
-    ERR_TIMEOUT, ERR_STATE = range(9)
+    ERR_TIMEOUT, ERR_STATE, ERR_TOO_LARGE = range(10)
 STATUS_NAMES = ["OK", "INVALID", "CUDA", "OOM", "NOT_PD", "NO_CONVERGENCE", "NONFINITE",
-                "TIMEOUT", "STATE"]
+                "TIMEOUT", "STATE", "TOO_LARGE"]
 FP64, MIXED = 0, 1
 
 
@@ -55,7 +55,8 @@ class Problem(C.Structure):
 EXPORTS = ["kot_default_options", "kot_create", "kot_destroy", "kot_last_error",
            "kot_build_features", "kot_set_features", "kot_get_features", "kot_residual",
            "kot_newton_direction", "kot_ssn_solve", "kot_get_history", "kot_batch_solve",
-           "kot_profile", "kot_profile_read", "kot_launch_count"]
+           "kot_profile", "kot_profile_read", "kot_launch_count",
+           "kot_embedding_sqnorm_noalloc"]
 
 KERNEL_CLASSES = ["gemm_f64", "jacobi_rotate", "jacobi_angles", "embed", "pair_sums", "gram",
                   "cholesky"]
