@@ -66,6 +66,9 @@ typedef struct {
   double jitter_max;       /* ... up to jitter_max * max_i K_ii                          */
   int use_eg;              /* 1: Algorithm 2 with the EG safeguard; 0: plain SSN steps   */
   int record_history;      /* 1: keep ||R(w_k)|| per iteration (kot_get_history)         */
+  int eig_ctas;            /* CTAs of the cooperative Jacobi eigensolver; 0 = one per SM  */
+  double mixed_switch;     /* mixed form: tensor-core Newton directions while ||R(w_k)|| > this;
+                              FP64 directions below it (default 1e-4)                     */
 } kot_options;
 
 typedef struct {
@@ -77,6 +80,8 @@ typedef struct {
   double ot_hat;           /* estimator OT-hat (Sec. 3)                                  */
   double eps;              /* Cholesky jitter used                                       */
   double seconds;          /* wall time of the call                                      */
+  int eig_calls;           /* symmetric eigen-decompositions performed by the solve      */
+  int eig_sweeps;          /* Jacobi sweeps summed over them                             */
 } kot_result;
 
 /* Fill *opt with the defaults listed above.  Returns KOT_ERR_INVALID if opt is NULL. */
@@ -157,9 +162,22 @@ typedef struct {
  * non-OK status among the problems (KOT_OK if all converged); each res[i].status is per problem. */
 kot_status kot_batch_solve(kot_ctx* ctx, int B, const kot_problem* probs, kot_result* res);
 
+/* ---- building block of the mixed form: dense product on the tensor cores ----
+ * C = alpha * op(A) * op(B)^T + beta * C, C: M x N (ldc), op(A): M x K, op(B): N x K, where
+ * op(X)(r, k) = X[r * ldx + k] (transX = 0) or X[k * ldx + r] (transX = 1).  FP64 in and out;
+ * the arithmetic runs on tcgen05 tensor cores in BF16 x BF16 -> FP32 with each operand split
+ * into `pieces` BF16 terms (1: BF16 accuracy, about 4e-3 relative; 3: about FP32 accuracy).
+ * This is how the mixed form computes the Jacobian-matvec products of Algorithm 1 (Sec. 4.3).
+ * Pointers follow the context's pointer mode.  KOT_ERR_TIMEOUT if a tensor-core wait gave up. */
+kot_status kot_dense_product(kot_ctx* ctx, int M, int N, int K, double alpha, const double* A,
+                             int lda, int transA, const double* B, int ldb, int transB,
+                             double beta, double* C, int ldc, int pieces);
+
 /* ---- tracing: per-kernel-class launch statistics (not part of the paper's method) ----
- * Kernel classes: 0 FP64 GEMM tiles, 1 Jacobi rotation round, 2 Jacobi angles, 3 kernel mean
- * embeddings, 4 embedding-norm pair sums, 5 Gram matrices Q and K, 6 Cholesky diagonal block.
+ * Kernel classes: 0 FP64 GEMM tiles, 1 Jacobi eigensolver (FP64, one launch per
+ * decomposition), 2 Jacobi eigensolver (FP32), 3 kernel mean
+ * embeddings, 4 embedding-norm pair sums, 5 Gram matrices Q and K, 6 Cholesky diagonal block,
+ * 7 tensor-core (tcgen05) GEMM tiles.
  * kot_profile(ctx, mask) turns on timing of the classes whose bit is set in mask (0 = off) and
  * clears the statistics.  While on, every launch of an enabled class is bracketed by CUDA events
  * on the context's stream.  kot_profile_read fills, for class cls, the number of launches, the

@@ -70,36 +70,39 @@ void Profiler::release() {
 
 namespace {
 
-constexpr int BM = 32, BN = 32, BK = 32, GT = 64;   // tile and threads per CTA
+constexpr int BK = 32, GT = 64;   // k-chunk and threads per CTA (8 x 8 thread grid)
 
-template <bool TA, bool TB>
+// Tile BT x BT (32 or 16); each thread owns a (BT/8) x (BT/8) strided sub-block.  The 16 x 16
+// variant is used when 32 x 32 tiles would leave most of the 152 SMs idle (l of a few hundred).
+template <int BT, bool TA, bool TB>
 __global__ void __launch_bounds__(GT) k_gemm_f64(int M, int N, int K, double alpha,
                                                  const double* __restrict__ A, int lda,
                                                  const double* __restrict__ B, int ldb,
                                                  const double* __restrict__ s, double beta,
                                                  double* __restrict__ C, int ldc, int flags) {
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  constexpr int TT = BT / 8;
+  const int m0 = blockIdx.y * BT, n0 = blockIdx.x * BT;
   if ((flags & G_SYM) && n0 < m0) return;
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
+  __shared__ double As[BK][BT + 1];
+  __shared__ double Bs[BK][BT + 1];
   int kbeg = 0, kend = K;
   if (flags & G_KLO_ROW) kbeg = max(kbeg, m0);
   if (flags & G_KLO_COL) kbeg = max(kbeg, n0);
-  if (flags & G_KHI_COL) kend = min(kend, n0 + BN);
-  if (flags & G_KHI_ROW) kend = min(kend, m0 + BM);
+  if (flags & G_KHI_COL) kend = min(kend, n0 + BT);
+  if (flags & G_KHI_ROW) kend = min(kend, m0 + BT);
   const int t = threadIdx.x, tx = t & 7, ty = t >> 3;
-  double acc[4][4];
+  double acc[TT][TT];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TT; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < TT; ++j) acc[i][j] = 0.0;
 
   for (int k0 = (kbeg / BK) * BK; k0 < kend; k0 += BK) {
 #pragma unroll 4
-    for (int r = 0; r < (BM * BK) / GT; ++r) {
+    for (int r = 0; r < (BT * BK) / GT; ++r) {
       int idx = t + r * GT;
       int m, k;
-      if (TA) { k = idx / BM; m = idx % BM; } else { m = idx / BK; k = idx % BK; }
+      if (TA) { k = idx / BT; m = idx % BT; } else { m = idx / BK; k = idx % BK; }
       int gm = m0 + m, gk = k0 + k;
       double v = 0.0;
       if (gm < M && gk >= kbeg && gk < kend) {
@@ -109,10 +112,10 @@ __global__ void __launch_bounds__(GT) k_gemm_f64(int M, int N, int K, double alp
       As[k][m] = v;
     }
 #pragma unroll 4
-    for (int r = 0; r < (BN * BK) / GT; ++r) {
+    for (int r = 0; r < (BT * BK) / GT; ++r) {
       int idx = t + r * GT;
       int n, k;
-      if (TB) { n = idx / BK; k = idx % BK; } else { k = idx / BN; n = idx % BN; }
+      if (TB) { n = idx / BK; k = idx % BK; } else { k = idx / BT; n = idx % BT; }
       int gn = n0 + n, gk = k0 + k;
       double v = 0.0;
       if (gn < N && gk >= kbeg && gk < kend)
@@ -122,25 +125,25 @@ __global__ void __launch_bounds__(GT) k_gemm_f64(int M, int N, int K, double alp
     __syncthreads();
 #pragma unroll 8
     for (int k = 0; k < BK; ++k) {
-      double a[4], b[4];
+      double a[TT], b[TT];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 8 * i];
+      for (int i = 0; i < TT; ++i) a[i] = As[k][ty + 8 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 8 * j];
+      for (int j = 0; j < TT; ++j) b[j] = Bs[k][tx + 8 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < TT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
   const bool mirror = (flags & G_SYM) && n0 > m0;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < TT; ++i) {
     int gm = m0 + ty + 8 * i;
     if (gm >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < TT; ++j) {
       int gn = n0 + tx + 8 * j;
       if (gn >= N) continue;
       double v = alpha * acc[i][j];
@@ -267,17 +270,27 @@ void gemm_f64(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alp
               const double* A, int lda, const double* B, int ldb, const double* s, double beta,
               double* C, int ldc, int flags) {
   if (M <= 0 || N <= 0) return;
-  dim3 grid(cdiv(N, BN), cdiv(M, BM));
+  // 32 x 32 tiles unless that gives fewer CTAs than about two per SM
+  const bool small = (size_t)cdiv(N, 32) * cdiv(M, 32) < 2 * 152;
+  const int BT = small ? 16 : 32;
+  dim3 grid(cdiv(N, BT), cdiv(M, BT));
   ProfScope ps(st, KC_GEMM_F64, 2.0 * M * N * (double)K, 8.0 * ((double)M * K + (double)K * N + (double)M * N));
   if (K <= 0) {   // C = beta C
     if (beta == 0.0)
       for (int i = 0; i < M; ++i) KOT_CUDA(cudaMemsetAsync(C + (size_t)i * ldc, 0, N * sizeof(double), st));
     return;
   }
-  if (!ta && !tb) k_gemm_f64<false, false><<<grid, GT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, s, beta, C, ldc, flags);
-  else if (!ta && tb) k_gemm_f64<false, true><<<grid, GT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, s, beta, C, ldc, flags);
-  else if (ta && !tb) k_gemm_f64<true, false><<<grid, GT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, s, beta, C, ldc, flags);
-  else k_gemm_f64<true, true><<<grid, GT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, s, beta, C, ldc, flags);
+#define KOT_GEMM_LAUNCH(BTV)                                                                      \
+  if (!ta && !tb) k_gemm_f64<BTV, false, false><<<grid, GT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, s, beta, C, ldc, flags); \
+  else if (!ta && tb) k_gemm_f64<BTV, false, true><<<grid, GT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, s, beta, C, ldc, flags); \
+  else if (ta && !tb) k_gemm_f64<BTV, true, false><<<grid, GT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, s, beta, C, ldc, flags); \
+  else k_gemm_f64<BTV, true, true><<<grid, GT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, s, beta, C, ldc, flags);
+  if (small) {
+    KOT_GEMM_LAUNCH(16)
+  } else {
+    KOT_GEMM_LAUNCH(32)
+  }
+#undef KOT_GEMM_LAUNCH
   KOT_CHECK_LAUNCH();
 }
 

@@ -7,8 +7,9 @@
 // takes a warm start: the SSN iteration hands in the eigenbasis of the previous, nearby Z, so
 // P^T Z P is already nearly diagonal and one or two sweeps finish the job.
 //
-// Each round updates every 2 x 2 block {p_a, q_a} x {p_b, q_b} of A in place (one thread per
-// block, the blocks are disjoint) and every row of V on the rotated columns.
+// Each round updates every 2 x 2 block {p_a, q_a} x {p_b, q_b} of A (one thread per block, the
+// blocks are disjoint) and every row of V on the rotated columns; the rotation of each pair is
+// the textbook 2 x 2 symmetric Schur step (Golub & Van Loan) that zeroes A_pq.
 #include <algorithm>
 #include <cmath>
 
@@ -20,128 +21,24 @@ namespace {
 
 inline int cdiv(size_t a, int b) { return (int)((a + b - 1) / b); }
 
-// Round-robin (circle method) pairing of lp indices: round r, slot k.
+// Round-robin (circle method) pairing of lp indices: round r in [0, lp-1), slot k in [0, lp/2).
+// Slot 0 pairs r with lp - 1; slot k > 0 pairs (r + k) mod m with (r - k) mod m, m = lp - 1.
 __device__ __forceinline__ void round_pair(int lp, int r, int k, int& p, int& q) {
   const int m = lp - 1;
   if (k == 0) {
     p = r;
     q = m;
   } else {
-    p = (r + k) % m;
-    q = (r - k + m) % m;
+    p = r + k;
+    if (p >= m) p -= m;
+    q = r - k;
+    if (q < 0) q += m;
   }
   if (p > q) {
-    int t = p;
+    const int t = p;
     p = q;
     q = t;
   }
-}
-
-// Rotation (c, s) that zeroes A_pq (Golub & Van Loan, symmetric Schur decomposition of a 2x2).
-__global__ void k_angles(int lp, int r, const double* __restrict__ A, double* __restrict__ rot,
-                         int* __restrict__ pairs) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= lp / 2) return;
-  int p, q;
-  round_pair(lp, r, k, p, q);
-  const double apq = A[(size_t)p * lp + q];
-  double c = 1.0, s = 0.0;
-  if (apq != 0.0) {
-    const double app = A[(size_t)p * lp + p], aqq = A[(size_t)q * lp + q];
-    const double tau = (aqq - app) / (2.0 * apq);
-    double t;
-    if (fabs(tau) > 1e150) t = 0.5 / tau;
-    else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-    c = 1.0 / sqrt(1.0 + t * t);
-    s = t * c;
-  }
-  rot[2 * k] = c;
-  rot[2 * k + 1] = s;
-  pairs[2 * k] = p;
-  pairs[2 * k + 1] = q;
-}
-
-// A <- J^T A J on every 2x2 block (pair a, pair b), b >= a, mirrored; V <- V J.
-// Blocks [0, nA) of the grid do A (2D tiles of 16 x 16 pair-blocks), the rest do V.
-__global__ void k_rotate(int lp, int l, int nApb, double* __restrict__ A, double* __restrict__ V,
-                         const double* __restrict__ rot, const int* __restrict__ pairs, int nAblk) {
-  const int half = lp / 2;
-  if ((int)blockIdx.x < nAblk) {
-    const int tilesPerRow = nApb;
-    const int ta = blockIdx.x / tilesPerRow, tb = blockIdx.x % tilesPerRow;
-    if (tb < ta) return;
-    const int a = ta * 16 + threadIdx.y, b = tb * 16 + threadIdx.x;
-    if (a >= half || b >= half || b < a) return;
-    const int pa = pairs[2 * a], qa = pairs[2 * a + 1], pb = pairs[2 * b], qb = pairs[2 * b + 1];
-    const double ca = rot[2 * a], sa = rot[2 * a + 1], cb = rot[2 * b], sb = rot[2 * b + 1];
-    const double m00 = A[(size_t)pa * lp + pb], m01 = A[(size_t)pa * lp + qb];
-    const double m10 = A[(size_t)qa * lp + pb], m11 = A[(size_t)qa * lp + qb];
-    // rows: p' = c p - s q ; q' = s p + c q
-    const double r00 = ca * m00 - sa * m10, r01 = ca * m01 - sa * m11;
-    const double r10 = sa * m00 + ca * m10, r11 = sa * m01 + ca * m11;
-    // columns: same map on the right
-    double n00 = cb * r00 - sb * r01, n01 = sb * r00 + cb * r01;
-    double n10 = cb * r10 - sb * r11, n11 = sb * r10 + cb * r11;
-    if (a == b) {
-      n01 = 0.0;   // the rotation zeroes this entry by construction
-      A[(size_t)pa * lp + pa] = n00;
-      A[(size_t)qa * lp + qa] = n11;
-      A[(size_t)pa * lp + qa] = 0.0;
-      A[(size_t)qa * lp + pa] = 0.0;
-      return;
-    }
-    A[(size_t)pa * lp + pb] = n00;
-    A[(size_t)pa * lp + qb] = n01;
-    A[(size_t)qa * lp + pb] = n10;
-    A[(size_t)qa * lp + qb] = n11;
-    A[(size_t)pb * lp + pa] = n00;
-    A[(size_t)qb * lp + pa] = n01;
-    A[(size_t)pb * lp + qa] = n10;
-    A[(size_t)qb * lp + qa] = n11;
-  } else {
-    // V: thread per (row i, pair b)
-    const size_t idx = (size_t)(blockIdx.x - nAblk) * 256 + threadIdx.y * 16 + threadIdx.x;
-    const size_t total = (size_t)l * half;
-    if (idx >= total) return;
-    const int i = (int)(idx / half), b = (int)(idx % half);
-    const int pb = pairs[2 * b], qb = pairs[2 * b + 1];
-    const double cb = rot[2 * b], sb = rot[2 * b + 1];
-    if (sb == 0.0 && cb == 1.0) return;
-    double* row = V + (size_t)i * lp;
-    const double vp = row[pb], vq = row[qb];
-    row[pb] = cb * vp - sb * vq;
-    row[qb] = sb * vp + cb * vq;
-  }
-}
-
-__global__ void k_offdiag_sumsq(int lp, const double* __restrict__ A, double* __restrict__ partial) {
-  __shared__ double sh[256];
-  double acc = 0.0;
-  const size_t n = (size_t)lp * lp;
-  for (size_t e = blockIdx.x * 256 + threadIdx.x; e < n; e += (size_t)gridDim.x * 256) {
-    int i = (int)(e / lp), j = (int)(e % lp);
-    if (i != j) acc = fma(A[e], A[e], acc);
-  }
-  sh[threadIdx.x] = acc;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
-}
-
-__global__ void k_sum2(int nb, const double* __restrict__ partial, double* __restrict__ out) {
-  __shared__ double sh[256];
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < nb; i += 256) acc += partial[i];
-  sh[threadIdx.x] = acc;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = sh[0];
 }
 
 // Place Z (l x l, ld l) into A (lp x lp) with a zero pad row/column; V = identity (or warm).
@@ -180,65 +77,352 @@ __global__ void k_gather(int l, int lp, const double* __restrict__ A, const doub
   if (i == 0) sig[rj] = A[(size_t)j * lp + j];
 }
 
+
+// ------------------------------------------------------------------ persistent variant
+// One cooperative launch runs every sweep.  Round r reads A_src and writes A_dst (double
+// buffer), updates V in place, and -- from A_src and the round-r angles alone -- computes the
+// round-(r+1) angles, so a single grid barrier separates rounds.  Cross-CTA data are read with
+// ld.global.cg (L2), and the barrier gives up after a bounded number of polls (error flag).
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+constexpr long long kBarrierPolls = 40000000;   // polls (>= 32 ns apart after the first 1024)
+
+__device__ __forceinline__ unsigned atom_add_acqrel_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+// Grid-wide barrier for a cooperative launch.  bar[0] counts arrivals and bar[1] holds the last
+// completed epoch; both are zeroed by the host before the launch and only grow, so no reset
+// races.  Arrival is one acquire-release atomic per CTA (it publishes the CTA's writes, ordered
+// before it by __syncthreads, and the last arriver, which sees count == epoch * nblocks,
+// publishes the epoch with a release store).  Returns false (and sets *err) if the wait gave up.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned& epoch, int* err) {
+  __shared__ int ok;
+  __syncthreads();
+  ++epoch;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    const unsigned arrived = atom_add_acqrel_u32(bar, 1u) + 1u;
+    if (arrived == epoch * nblocks) {
+      st_release_u32(bar + 1, epoch);
+    } else {
+      long long polls = 0;
+      while ((int)(ld_acquire_u32(bar + 1) - epoch) < 0) {
+        if (++polls > kBarrierPolls) {
+          atomicExch(err, 1);
+          ok = 0;
+          break;
+        }
+        if (polls > 1024) __nanosleep(32);
+      }
+    }
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <typename T>
+struct CoopArgs {
+  int lp, l, max_sweeps;
+  T* A0;
+  T* A1;
+  T* V;
+  T* rot0;             // round-parity 0 angles (c, s) per pair
+  T* rot1;
+  double* partial;     // gridDim.x partial sums
+  unsigned* bar;       // [count, generation]
+  int* err;
+  int* sweeps_out;
+  double tol_rel;      // stop when off(A) <= tol_rel * ||A||_F
+  double floor_rel;    // ... or when a sweep stalls (off > 0.5 prev) below floor_rel * ||A||_F
+};
+
+template <typename T>
+__device__ __forceinline__ void rot_angle(T app, T aqq, T apq, T& c, T& s) {
+  c = T(1);
+  s = T(0);
+  if (apq != T(0)) {
+    const T tau = (aqq - app) / (T(2) * apq);
+    T t;
+    if (fabs((double)tau) > 1e150) t = T(0.5) / tau;
+    else t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+    c = T(1) / sqrt(T(1) + t * t);
+    s = t * c;
+  }
+}
+
+// New 2x2 block J_a^T M J_b (rows p_a, q_a; columns p_b, q_b).
+template <typename T>
+__device__ __forceinline__ void rot_block(T ca, T sa, T cb, T sb, T m00, T m01, T m10, T m11,
+                                          T& n00, T& n01, T& n10, T& n11) {
+  const T r00 = ca * m00 - sa * m10, r01 = ca * m01 - sa * m11;
+  const T r10 = sa * m00 + ca * m10, r11 = sa * m01 + ca * m11;
+  n00 = cb * r00 - sb * r01;
+  n01 = sb * r00 + cb * r01;
+  n10 = cb * r10 - sb * r11;
+  n11 = sb * r10 + cb * r11;
+}
+
+// Slot of the round-r pair that contains index i (inverse of round_pair).
+__device__ __forceinline__ int slot_of(int lp, int r, int i) {
+  const int m = lp - 1;
+  if (i == m || i == r) return 0;
+  int k = i - r;
+  if (k < 0) k += m;
+  if (k >= lp / 2) k = m - k;
+  return k;
+}
+
+template <typename T>
+__device__ double block_reduce_sum(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+constexpr int kCoopThreads = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(kCoopThreads) k_jacobi_coop(CoopArgs<T> a) {
+  __shared__ double sh[kCoopThreads];
+  const int lp = a.lp, l = a.l, half = lp / 2;
+  const unsigned nb = gridDim.x;
+  const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t gstride = (size_t)gridDim.x * blockDim.x;
+  T* A[2] = {a.A0, a.A1};
+  T* rot[2] = {a.rot0, a.rot1};
+  int cur = 0;
+  unsigned epoch = 0;   // barriers passed (identical in every CTA)
+
+  // deterministic sum of a per-block partial over the grid (every block gets the same value)
+  // (two halves of the partial array alternate, so a block still reading one sum's partials
+  // never sees them overwritten by the next sum's)
+  int sum_calls = 0;
+  auto grid_sum = [&](double v, bool& ok) -> double {
+    double* part = a.partial + (size_t)(sum_calls++ & 1) * nb;
+    double bs = block_reduce_sum<T>(v, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+    ok = grid_barrier(a.bar, nb, epoch, a.err);
+    double tot = 0.0;
+    for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) tot += __ldcg(part + i);
+    tot = block_reduce_sum<T>(tot, sh);
+    return tot;
+  };
+
+  // round-0 angles and ||A||_F^2
+  double acc = 0.0;
+  for (size_t e = gtid; e < (size_t)lp * lp; e += gstride) {
+    const double v = (double)__ldcg(A[0] + e);
+    acc += v * v;
+  }
+  for (size_t k = gtid; k < (size_t)half; k += gstride) {
+    int p, q;
+    round_pair(lp, 0, (int)k, p, q);
+    T c, s;
+    rot_angle<T>(__ldcg(A[0] + (size_t)p * lp + p), __ldcg(A[0] + (size_t)q * lp + q),
+                 __ldcg(A[0] + (size_t)p * lp + q), c, s);
+    rot[0][2 * k] = c;
+    rot[0][2 * k + 1] = s;
+  }
+  bool ok = true;
+  const double nrm2 = grid_sum(acc, ok);
+  if (!ok) return;
+  double prev_off = INFINITY;
+  int sweep = 0;
+  unsigned gr = 0;   // rounds executed so far: round gr uses angles rot[gr & 1]
+  for (;; ++sweep) {
+    // off-diagonal norm of the current A
+    acc = 0.0;
+    for (int e = (int)gtid; e < lp * lp; e += (int)gstride) {
+      const int i = e / lp, j = e - i * lp;
+      if (i != j) {
+        const double v = (double)__ldcg(A[cur] + e);
+        acc += v * v;
+      }
+    }
+    const double off2 = grid_sum(acc, ok);
+    if (!ok) return;
+    const double off = sqrt(off2), nrm = sqrt(nrm2);
+    if (!(off > a.tol_rel * nrm) || nrm == 0.0) break;
+    if (sweep >= 2 && off > 0.5 * prev_off && off <= a.floor_rel * nrm) break;
+    if (sweep >= a.max_sweeps) {
+      if (gtid == 0) atomicExch(a.err, 2);       // not converged
+      break;
+    }
+    prev_off = off;
+    for (int r = 0; r < lp - 1; ++r) {
+      const T* src = A[cur];
+      T* dst = A[cur ^ 1];
+      const T* rc = rot[gr & 1];
+      T* rn = rot[(gr + 1) & 1];
+      const int rnext = (r + 1 == lp - 1) ? 0 : r + 1;
+      const int nA = half * half, nV = l * half, nN = half;
+      for (int it = (int)gtid; it < nA + nV + nN; it += (int)gstride) {
+        if (it < nA) {
+          const int ia = it / half, ib = it - ia * half;
+          if (ib < ia) continue;
+          int pa, qa, pb, qb;
+          round_pair(lp, r, ia, pa, qa);
+          round_pair(lp, r, ib, pb, qb);
+          const T ca = __ldcg(rc + 2 * ia), sa = __ldcg(rc + 2 * ia + 1);
+          const T cb = __ldcg(rc + 2 * ib), sb = __ldcg(rc + 2 * ib + 1);
+          T n00, n01, n10, n11;
+          rot_block<T>(ca, sa, cb, sb, __ldcg(src + (size_t)pa * lp + pb), __ldcg(src + (size_t)pa * lp + qb),
+                       __ldcg(src + (size_t)qa * lp + pb), __ldcg(src + (size_t)qa * lp + qb),
+                       n00, n01, n10, n11);
+          if (ia == ib) {
+            dst[(size_t)pa * lp + pa] = n00;
+            dst[(size_t)qa * lp + qa] = n11;
+            dst[(size_t)pa * lp + qa] = T(0);
+            dst[(size_t)qa * lp + pa] = T(0);
+          } else {
+            dst[(size_t)pa * lp + pb] = n00;
+            dst[(size_t)pa * lp + qb] = n01;
+            dst[(size_t)qa * lp + pb] = n10;
+            dst[(size_t)qa * lp + qb] = n11;
+            dst[(size_t)pb * lp + pa] = n00;
+            dst[(size_t)qb * lp + pa] = n01;
+            dst[(size_t)pb * lp + qa] = n10;
+            dst[(size_t)qb * lp + qa] = n11;
+          }
+        } else if (it < nA + nV) {
+          const int v = it - nA;
+          const int i = v / half, b = v - i * half;
+          int pb, qb;
+          round_pair(lp, r, b, pb, qb);
+          const T cb = __ldcg(rc + 2 * b), sb = __ldcg(rc + 2 * b + 1);
+          if (sb == T(0) && cb == T(1)) continue;
+          T* row = a.V + (size_t)i * lp;
+          const T vp = __ldcg(row + pb), vq = __ldcg(row + qb);
+          row[pb] = cb * vp - sb * vq;
+          row[qb] = sb * vp + cb * vq;
+        } else {
+          // angle of next-round pair k from the values this round writes, recomputed here
+          const int k = it - nA - nV;
+          int pn, qn;
+          round_pair(lp, rnext, k, pn, qn);
+          const int sp = slot_of(lp, r, pn), sq = slot_of(lp, r, qn);
+          int pp, qp, pq_, qq;
+          round_pair(lp, r, sp, pp, qp);
+          round_pair(lp, r, sq, pq_, qq);
+          const T cp = __ldcg(rc + 2 * sp), spn = __ldcg(rc + 2 * sp + 1);
+          const T cq = __ldcg(rc + 2 * sq), sqn = __ldcg(rc + 2 * sq + 1);
+          // diagonal entries of pn and qn after this round
+          T d00, d01, d10, d11, app, aqq, apq;
+          rot_block<T>(cp, spn, cp, spn, __ldcg(src + (size_t)pp * lp + pp), __ldcg(src + (size_t)pp * lp + qp),
+                       __ldcg(src + (size_t)qp * lp + pp), __ldcg(src + (size_t)qp * lp + qp), d00, d01, d10, d11);
+          app = (pn == pp) ? d00 : d11;
+          rot_block<T>(cq, sqn, cq, sqn, __ldcg(src + (size_t)pq_ * lp + pq_), __ldcg(src + (size_t)pq_ * lp + qq),
+                       __ldcg(src + (size_t)qq * lp + pq_), __ldcg(src + (size_t)qq * lp + qq), d00, d01, d10, d11);
+          aqq = (qn == pq_) ? d00 : d11;
+          // off-diagonal entry (pn, qn): block (slot sp rows) x (slot sq columns)
+          if (sp == sq) {
+            apq = T(0);
+          } else {
+            rot_block<T>(cp, spn, cq, sqn, __ldcg(src + (size_t)pp * lp + pq_), __ldcg(src + (size_t)pp * lp + qq),
+                         __ldcg(src + (size_t)qp * lp + pq_), __ldcg(src + (size_t)qp * lp + qq), d00, d01, d10, d11);
+            apq = (pn == pp) ? ((qn == pq_) ? d00 : d01) : ((qn == pq_) ? d10 : d11);
+          }
+          T c, s;
+          rot_angle<T>(app, aqq, apq, c, s);
+          rn[2 * k] = c;
+          rn[2 * k + 1] = s;
+        }
+      }
+      if (!grid_barrier(a.bar, nb, epoch, a.err)) return;
+      cur ^= 1;
+      ++gr;
+    }
+  }
+  if (gtid == 0) a.sweeps_out[0] = sweep * 2 + cur;   // sweeps and the buffer holding A
+}
 }  // namespace
 
 int eig_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, double* P,
-                double* sig, JacobiWork& w, int max_sweeps, double* host_scal) {
-  const int lp = std::max(2, l + (l & 1));   // even, >= 2
+                double* sig, JacobiWork& w, int max_sweeps, double* host_scal, int ctas) {
+  const int lp = std::max(2, l + (l & 1));   // even, >= 2; a zero pad row/column never rotates
   const int half = lp / 2;
-  w.A.alloc((size_t)lp * lp);
+  int dev = 0, nsm = 0, per_sm = 0;
+  KOT_CUDA(cudaGetDevice(&dev));
+  KOT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  KOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_coop<double>, kCoopThreads, 0));
+  if (per_sm < 1) throw Error{KOT_ERR_CUDA, "eig: cooperative kernel does not fit on an SM"};
+  // one CTA per SM by default (fewer arrivals per barrier than several per SM)
+  const int grid = ctas > 0 ? std::min(ctas, nsm * per_sm) : nsm;
+  w.A.alloc(2 * (size_t)lp * lp);
   w.V.alloc((size_t)lp * lp);
-  w.rot.alloc((size_t)lp);
-  w.pairs.alloc((size_t)lp);
+  w.rot.alloc(2 * (size_t)lp);
   w.rank.alloc((size_t)l);
-  w.partial.alloc(kReduceBlocks);
+  w.partial.alloc(std::max<size_t>(kReduceBlocks, 2 * (size_t)grid));
   w.scal.alloc(4);
+  w.bar.alloc(2);
+  KOT_CUDA(cudaMemsetAsync(w.bar.p, 0, 2 * sizeof(unsigned), st));   // counters start at 0
+  w.flags.alloc(2);
+  KOT_CUDA(cudaMemsetAsync(w.flags.p, 0, 2 * sizeof(int), st));
+  double* A0 = w.A.p;
+  double* A1 = w.A.p + (size_t)lp * lp;
   dim3 g2(cdiv(lp, 32), cdiv(lp, 8)), b2(32, 8);
   if (warm) {
-    // A = warm^T Z warm: first V(:, :l) = Z warm (ld lp), then A = warm^T V
+    // A = warm^T Z warm: V(:, :l) = Z warm (ld lp), then A0 = warm^T V
     gemm_f64(st, false, false, l, l, l, 1.0, Z, l, warm, l, nullptr, 0.0, w.V.p, lp, 0);
-    gemm_f64(st, true, false, l, l, l, 1.0, warm, l, w.V.p, lp, nullptr, 0.0, w.A.p, lp, G_SYM);
-    k_init_pad<<<g2, b2, 0, st>>>(l, lp, w.A.p, w.V.p, nullptr, warm);
+    gemm_f64(st, true, false, l, l, l, 1.0, warm, l, w.V.p, lp, nullptr, 0.0, A0, lp, G_SYM);
+    k_init_pad<<<g2, b2, 0, st>>>(l, lp, A0, w.V.p, nullptr, warm);
   } else {
-    k_init_pad<<<g2, b2, 0, st>>>(l, lp, w.A.p, w.V.p, Z, nullptr);
+    k_init_pad<<<g2, b2, 0, st>>>(l, lp, A0, w.V.p, Z, nullptr);
   }
   KOT_CHECK_LAUNCH();
-  // ||A||_F^2 for the stopping test
-  sumsq_f64(st, (size_t)lp * lp, w.A.p, w.scal.p + 1, w.partial.p);
-  const int nApb = cdiv(half, 16);
-  const int nAblk = nApb * nApb;
-  const int nVblk = cdiv((size_t)l * half, 256);
-  int sweeps = 0;
-  double prev_off = INFINITY;
-  for (; sweeps <= max_sweeps; ++sweeps) {
-    k_offdiag_sumsq<<<kReduceBlocks, 256, 0, st>>>(lp, w.A.p, w.partial.p);
-    k_sum2<<<1, 256, 0, st>>>(kReduceBlocks, w.partial.p, w.scal.p);
-    KOT_LAUNCHED(2);
-    KOT_CUDA(cudaMemcpyAsync(host_scal, w.scal.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    KOT_CUDA(cudaStreamSynchronize(st));
-    const double off = std::sqrt(host_scal[0]), nrm = std::sqrt(host_scal[1]);
-    if (!std::isfinite(off)) throw Error{KOT_ERR_NONFINITE, "eig: non-finite matrix"};
-    if (off <= 1e-14 * nrm || nrm == 0.0) break;
-    if (sweeps >= 2 && off > 0.5 * prev_off && off <= 1e-12 * nrm) break;   // at rounding floor
-    if (sweeps == max_sweeps) throw Error{KOT_ERR_NO_CONVERGENCE, "eig: Jacobi did not converge"};
-    prev_off = off;
-    // algorithmic work of one round: 24 flops per rotated 2x2 block of A (upper half of the
-    // half x half block grid), 6 per (row, pair) of V; bytes: each touched double read + written
+  CoopArgs<double> a;
+  a.lp = lp;
+  a.l = l;
+  a.max_sweeps = max_sweeps;
+  a.A0 = A0;
+  a.A1 = A1;
+  a.V = w.V.p;
+  a.rot0 = w.rot.p;
+  a.rot1 = w.rot.p + lp;
+  a.partial = w.partial.p;
+  a.bar = w.bar.p;
+  a.err = w.flags.p;
+  a.sweeps_out = w.flags.p + 1;
+  a.tol_rel = 1e-14;
+  a.floor_rel = 1e-12;
+  {
+    // algorithmic work of one sweep: (lp - 1) rounds of 24 flops per 2x2 block of A over the
+    // upper half of the (lp/2)^2 blocks and 6 flops per (row, pair) of V
     const double hb = (double)half * (half + 1) / 2.0;
     const double rflops = 24.0 * hb + 6.0 * (double)l * half;
-    const double rbytes = 16.0 * (4.0 * hb + 4.0 * hb) + 16.0 * 2.0 * (double)l * half;
-    for (int r = 0; r < lp - 1; ++r) {
-      {
-        ProfScope ps(st, KC_JACOBI_ANGLES, 0.0, 16.0 * 3 * half);
-        k_angles<<<cdiv(half, 128), 128, 0, st>>>(lp, r, w.A.p, w.rot.p, w.pairs.p);
-      }
-      ProfScope ps(st, KC_JACOBI_ROTATE, rflops, rbytes);
-      k_rotate<<<nAblk + nVblk, dim3(16, 16), 0, st>>>(lp, l, nApb, w.A.p, w.V.p, w.rot.p, w.pairs.p, nAblk);
-    }
-    KOT_LAUNCHED(2 * (lp - 1));
+    ProfScope ps(st, KC_JACOBI, rflops * (lp - 1), 8.0 * 2.0 * (2.0 * lp * (double)lp + (double)l * lp));
+    void* args[] = {&a};
+    KOT_CUDA(cudaLaunchCooperativeKernel((const void*)k_jacobi_coop<double>, dim3(grid), dim3(kCoopThreads),
+                                         args, 0, st));
+    KOT_LAUNCHED(1);
   }
-  k_rank<<<cdiv(l, 128), 128, 0, st>>>(l, lp, w.A.p, w.rank.p);
-  k_gather<<<dim3(cdiv(l, 32), cdiv(l, 8)), b2, 0, st>>>(l, lp, w.A.p, w.V.p, w.rank.p, P, sig);
+  int hflags[2] = {0, 0};
+  KOT_CUDA(cudaMemcpyAsync(hflags, w.flags.p, sizeof(hflags), cudaMemcpyDeviceToHost, st));
+  KOT_CUDA(cudaStreamSynchronize(st));
+  (void)host_scal;
+  if (hflags[0] == 1) throw Error{KOT_ERR_TIMEOUT, "eig: grid barrier timed out"};
+  if (hflags[0] == 2) throw Error{KOT_ERR_NO_CONVERGENCE, "eig: Jacobi did not converge"};
+  const int sweeps = hflags[1] / 2, cur = hflags[1] & 1;
+  const double* Af = cur ? A1 : A0;
+  k_rank<<<cdiv(l, 128), 128, 0, st>>>(l, lp, Af, w.rank.p);
+  k_gather<<<dim3(cdiv(l, 32), cdiv(l, 8)), b2, 0, st>>>(l, lp, Af, w.V.p, w.rank.p, P, sig);
   KOT_LAUNCHED(2);
   return sweeps;
 }

@@ -63,6 +63,9 @@ struct kot_ctx {
   double* hs = nullptr;                        // pinned host scalars
   int* hi = nullptr;
   JacobiWork jw;
+  TcWork tc;
+  bool force64 = false;   // mixed form: run the Newton-direction products in FP64 for now
+  long long eig_calls = 0, eig_sweeps = 0;
   std::vector<double> hist;
   Profiler prof;
 };
@@ -94,6 +97,8 @@ void set_defaults(kot_options* o) {
   o->jitter_max = 1e-6;
   o->use_eg = 1;
   o->record_history = 0;
+  o->eig_ctas = 0;
+  o->mixed_switch = 1e-4;
 }
 
 bool pos_finite(double v) { return std::isfinite(v) && v > 0.0; }
@@ -157,6 +162,27 @@ void phi(kot_ctx* C, const double* X, double* out, double* tmp) {
   coldot_upper(C->st, l, C->R.p, tmp, out);
 }
 
+// ---- the same operators on the tensor cores (mixed form, Newton direction only) ----
+bool mixed(const kot_ctx* C) { return C->opt.precision == KOT_MIXED && !C->force64; }
+constexpr int kPieces = 3;   // BF16 pieces per operand: about FP32 accuracy
+
+void phi_star_nd(kot_ctx* C, const double* gamma, double* out) {
+  if (!mixed(C)) return phi_star(C, gamma, out);
+  const int l = C->l;
+  // out[m][n] = sum_k R[m][k] gamma_k R[n][k]
+  gemm_tc(C->st, C->tc, l, l, l, TcOperand{C->R.p, l, false, gamma}, TcOperand{C->R.p, l, false, nullptr},
+          kPieces, 1.0, 0.0, out, l);
+}
+
+void phi_nd(kot_ctx* C, const double* X, double* out, double* tmp) {
+  if (!mixed(C)) return phi(C, X, out, tmp);
+  const int l = C->l;
+  // tmp = X R: tmp[m][n] = sum_k X[m][k] R[k][n]
+  gemm_tc(C->st, C->tc, l, l, l, TcOperand{X, l, false, nullptr}, TcOperand{C->R.p, l, true, nullptr},
+          kPieces, 1.0, 0.0, tmp, l);
+  coldot_upper(C->st, l, C->R.p, tmp, out);
+}
+
 // out = (Q gamma - z)/(2 lambda2) - Phi(X)
 void grad_gamma(kot_ctx* C, const double* gamma, const double* X, double* out, double* vtmp,
                 double* mtmp) {
@@ -173,7 +199,9 @@ void grad_gamma(kot_ctx* C, const double* gamma, const double* X, double* out, d
 void eig_into(kot_ctx* C, const double* Z, EigSlot& e, const EigSlot* warm) {
   const int l = C->l;
   const double* wp = (warm && warm->valid) ? warm->P.p : nullptr;
-  eig_sym_f64(C->st, l, Z, wp, e.P.p, e.sig.p, C->jw, kMaxSweeps, C->hs);
+  C->eig_sweeps += eig_sym_f64(C->st, l, Z, wp, e.P.p, e.sig.p, C->jw, kMaxSweeps, C->hs,
+                               C->opt.eig_ctas);
+  C->eig_calls += 1;
   count_nonpos(C->st, l, e.sig.p, C->iscal.p);
   KOT_CUDA(cudaMemcpyAsync(C->hi, C->iscal.p, sizeof(int), cudaMemcpyDeviceToHost, C->st));
   KOT_CUDA(cudaStreamSynchronize(C->st));
@@ -245,18 +273,39 @@ void t_apply(kot_ctx* C, const EigSlot& e, double mu, const double* S, double* o
   const bool comp = na > nb;
   const int rows = comp ? nb : na;
   const double* Ps = comp ? e.P.p : e.P.p + nb;   // l x rows, ld l
-  gemm_f64(C->st, true, false, rows, l, l, 1.0, Ps, l, S, l, nullptr, 0.0, C->TU.p, l, 0);
-  gemm_f64(C->st, false, false, rows, l, l, 1.0, C->TU.p, l, e.P.p, l, nullptr, 0.0, C->TV.p, l, 0);
-  t_weights(C->st, l, nb, e.sig.p, mu, comp ? 1 : 0, C->TV.p);
-  gemm_f64(C->st, false, true, rows, l, l, 1.0, C->TV.p, l, e.P.p, l, nullptr, 0.0, C->TW.p, l, 0);
-  gemm_f64(C->st, false, false, l, l, rows, 1.0, Ps, l, C->TW.p, l, nullptr, 0.0, C->TG.p, l, 0);
+  if (mixed(C)) {
+    cudaStream_t st = C->st;
+    TcWork& w = C->tc;
+    // U = Ps^T S ; V = U P ; weights ; W = V P^T ; G = Ps W   (C = op(A) op(B)^T form)
+    gemm_tc(st, w, rows, l, l, TcOperand{Ps, l, true, nullptr}, TcOperand{S, l, true, nullptr}, kPieces, 1.0,
+            0.0, C->TU.p, l);
+    gemm_tc(st, w, rows, l, l, TcOperand{C->TU.p, l, false, nullptr}, TcOperand{e.P.p, l, true, nullptr},
+            kPieces, 1.0, 0.0, C->TV.p, l);
+    t_weights(st, l, nb, e.sig.p, mu, comp ? 1 : 0, C->TV.p);
+    gemm_tc(st, w, rows, l, l, TcOperand{C->TV.p, l, false, nullptr}, TcOperand{e.P.p, l, false, nullptr},
+            kPieces, 1.0, 0.0, C->TW.p, l);
+    gemm_tc(st, w, l, l, rows, TcOperand{Ps, l, false, nullptr}, TcOperand{C->TW.p, l, true, nullptr},
+            kPieces, 1.0, 0.0, C->TG.p, l);
+  } else {
+    gemm_f64(C->st, true, false, rows, l, l, 1.0, Ps, l, S, l, nullptr, 0.0, C->TU.p, l, 0);
+    gemm_f64(C->st, false, false, rows, l, l, 1.0, C->TU.p, l, e.P.p, l, nullptr, 0.0, C->TV.p, l, 0);
+    t_weights(C->st, l, nb, e.sig.p, mu, comp ? 1 : 0, C->TV.p);
+    gemm_f64(C->st, false, true, rows, l, l, 1.0, C->TV.p, l, e.P.p, l, nullptr, 0.0, C->TW.p, l, 0);
+    gemm_f64(C->st, false, false, l, l, rows, 1.0, Ps, l, C->TW.p, l, nullptr, 0.0, C->TG.p, l, 0);
+  }
   sym_sum(C->st, l, C->TG.p, S, 1.0 / mu, comp ? 1 : 0, out);
 }
 
 // Algorithm 1 at w (residual r, eigen-decomposition e).  Returns CG iterations.
+// Mixed form: the products run on the tensor cores; if CG reaches its cap without meeting the
+// test of Eq. (4.3) (the products' ~1e-7 error times the Schur system's condition ~1/mu leaves
+// it short near the solution), the direction is refined in FP64: the right-hand side is
+// recomputed, the true residual a1 - H x of the mixed solution is formed, and CG continues from
+// that x with FP64 products for up to cg_max_iter more iterations.
 int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu, double cg_tol_abs,
-                     double* dgam, double* dX) {
+                     double* dgam, double* dX, bool allow_tc) {
   const int l = C->l;
+  C->force64 = !allow_tc;
   const size_t L2 = (size_t)l * l;
   cudaStream_t st = C->st;
   double* rT = C->M1.p;     // r2 + T[r2]
@@ -266,60 +315,89 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
   double* ev = C->v3.p;     // CG residual
   double* pv = C->v4.p;     // CG direction
   double* Hp = C->v6.p;
-  t_apply(C, e, mu, r.r2.p, rT);
-  axpby(st, L2, 1.0, r.r2.p, 1.0, rT, rT);
-  phi(C, rT, C->v1.p, C->M2.p);
-  axpby(st, l, -1.0, r.r1.p, -1.0 / (mu + 1.0), C->v1.p, a1);
-  axpby(st, L2, -1.0 / (mu + 1.0), rT, 0.0, nullptr, at2);
-  fill(st, l, 0.0, dgam);
-  fill(st, L2, 0.0, TPx);
-  KOT_CUDA(cudaMemcpyAsync(ev, a1, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  KOT_CUDA(cudaMemcpyAsync(pv, a1, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
   const int cap = cg_tol_abs > 0 ? 10 * l + 50 : C->opt.cg_max_iter;
-  int it = 0;
-  double ee = 0;
-  while (true) {
-    // stop test at the current iterate: ||e|| vs tau min(1, kappa ||r|| ||dw||)
-    sumsq_f64(st, l, ev, C->scal.p, C->partial.p);
-    sumsq_f64(st, l, dgam, C->scal.p + 1, C->partial.p);
-    axpby(st, L2, 1.0, at2, -1.0, TPx, C->M5.p);
-    sumsq_f64(st, L2, C->M5.p, C->scal.p + 2, C->partial.p);
-    fetch(C, 3);
-    ee = C->hs[0];
-    const double enorm = std::sqrt(ee);
-    if (!std::isfinite(enorm)) fail(KOT_ERR_NONFINITE, "CG residual is not finite");
-    bool stop;
-    if (cg_tol_abs > 0) stop = enorm <= cg_tol_abs;
-    else {
-      const double dw = std::sqrt(C->hs[1]) + std::sqrt(C->hs[2]);
-      stop = enorm <= C->opt.tau * std::min(1.0, C->opt.kappa * r.norm * dw);
+  const bool refine = mixed(C);
+  int total = 0;
+  bool met = false;
+  for (int phase = 0; phase < (refine ? 2 : 1); ++phase) {
+    if (phase == 1) {
+      if (met) break;
+      C->force64 = true;
     }
-    if (stop || it >= cap) break;
-    // Hp = Q p/(2 lambda2) + mu p + Phi(T[Phi*(p)])
-    phi_star(C, pv, C->M5.p);
-    t_apply(C, e, mu, C->M5.p, C->M6.p);
-    phi(C, C->M6.p, C->v5.p, C->M5.p);
-    gemv_f64(st, l, 1.0 / (2.0 * C->lambda2), C->Q.p, pv, 0.0, Hp);
-    axpby(st, l, mu, pv, 1.0, Hp, Hp);
-    axpby(st, l, 1.0, Hp, 1.0, C->v5.p, Hp);
-    dot_f64(st, l, pv, Hp, C->scal.p + 3, C->partial.p);
-    KOT_CUDA(cudaMemcpyAsync(C->hs + 3, C->scal.p + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
-    KOT_CUDA(cudaStreamSynchronize(st));
-    const double pHp = C->hs[3];
-    if (!(pHp > 0.0)) break;
-    const double a = ee / pHp;
-    axpby(st, l, 1.0, dgam, a, pv, dgam);
-    axpby(st, L2, 1.0, TPx, a, C->M6.p, TPx);
-    axpby(st, l, 1.0, ev, -a, Hp, ev);
-    sumsq_f64(st, l, ev, C->scal.p + 4, C->partial.p);
-    KOT_CUDA(cudaMemcpyAsync(C->hs + 4, C->scal.p + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
-    KOT_CUDA(cudaStreamSynchronize(st));
-    const double beta = C->hs[4] / ee;
-    axpby(st, l, 1.0, ev, beta, pv, pv);
-    ++it;
+    // right-hand side: a1 = -r1 - Phi(r2 + T[r2])/(mu+1), at2 = -(r2 + T[r2])/(mu+1)
+    t_apply(C, e, mu, r.r2.p, rT);
+    axpby(st, L2, 1.0, r.r2.p, 1.0, rT, rT);
+    phi_nd(C, rT, C->v1.p, C->M2.p);
+    axpby(st, l, -1.0, r.r1.p, -1.0 / (mu + 1.0), C->v1.p, a1);
+    axpby(st, L2, -1.0 / (mu + 1.0), rT, 0.0, nullptr, at2);
+    if (phase == 0) {
+      fill(st, l, 0.0, dgam);
+      fill(st, L2, 0.0, TPx);
+      KOT_CUDA(cudaMemcpyAsync(ev, a1, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+      // e = a1 - H x with FP64 products, and T[Phi*(x)] recomputed alongside
+      phi_star_nd(C, dgam, C->M5.p);
+      t_apply(C, e, mu, C->M5.p, TPx);
+      phi_nd(C, TPx, C->v5.p, C->M5.p);
+      gemv_f64(st, l, 1.0 / (2.0 * C->lambda2), C->Q.p, dgam, 0.0, Hp);
+      axpby(st, l, mu, dgam, 1.0, Hp, Hp);
+      axpby(st, l, 1.0, Hp, 1.0, C->v5.p, Hp);
+      axpby(st, l, 1.0, a1, -1.0, Hp, ev);
+    }
+    KOT_CUDA(cudaMemcpyAsync(pv, ev, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    int it = 0;
+    double ee = 0;
+    while (true) {
+      // stop test at the current iterate: ||e|| vs tau min(1, kappa ||r|| ||dw||)
+      sumsq_f64(st, l, ev, C->scal.p, C->partial.p);
+      sumsq_f64(st, l, dgam, C->scal.p + 1, C->partial.p);
+      axpby(st, L2, 1.0, at2, -1.0, TPx, C->M5.p);
+      sumsq_f64(st, L2, C->M5.p, C->scal.p + 2, C->partial.p);
+      fetch(C, 3);
+      ee = C->hs[0];
+      const double enorm = std::sqrt(ee);
+      if (!std::isfinite(enorm)) {
+        C->force64 = false;
+        fail(KOT_ERR_NONFINITE, "CG residual is not finite");
+      }
+      bool stop;
+      if (cg_tol_abs > 0) stop = enorm <= cg_tol_abs;
+      else {
+        const double dw = std::sqrt(C->hs[1]) + std::sqrt(C->hs[2]);
+        stop = enorm <= C->opt.tau * std::min(1.0, C->opt.kappa * r.norm * dw);
+      }
+      met = stop;
+      if (stop || it >= cap) break;
+      // Hp = Q p/(2 lambda2) + mu p + Phi(T[Phi*(p)])
+      phi_star_nd(C, pv, C->M5.p);
+      t_apply(C, e, mu, C->M5.p, C->M6.p);
+      phi_nd(C, C->M6.p, C->v5.p, C->M5.p);
+      gemv_f64(st, l, 1.0 / (2.0 * C->lambda2), C->Q.p, pv, 0.0, Hp);
+      axpby(st, l, mu, pv, 1.0, Hp, Hp);
+      axpby(st, l, 1.0, Hp, 1.0, C->v5.p, Hp);
+      dot_f64(st, l, pv, Hp, C->scal.p + 3, C->partial.p);
+      KOT_CUDA(cudaMemcpyAsync(C->hs + 3, C->scal.p + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+      KOT_CUDA(cudaStreamSynchronize(st));
+      const double pHp = C->hs[3];
+      if (!(pHp > 0.0)) break;
+      const double a = ee / pHp;
+      axpby(st, l, 1.0, dgam, a, pv, dgam);
+      axpby(st, L2, 1.0, TPx, a, C->M6.p, TPx);
+      axpby(st, l, 1.0, ev, -a, Hp, ev);
+      sumsq_f64(st, l, ev, C->scal.p + 4, C->partial.p);
+      KOT_CUDA(cudaMemcpyAsync(C->hs + 4, C->scal.p + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+      KOT_CUDA(cudaStreamSynchronize(st));
+      const double beta = C->hs[4] / ee;
+      axpby(st, l, 1.0, ev, beta, pv, pv);
+      ++it;
+    }
+    total += it;
   }
+  C->force64 = false;
   axpby(st, L2, 1.0, at2, -1.0, TPx, dX);
-  return it;
+  if (C->opt.precision == KOT_MIXED && gemm_tc_error(st, C->tc))
+    fail(KOT_ERR_TIMEOUT, "tensor-core GEMM wait timed out");
+  return total;
 }
 
 // One projected extragradient step on (vg, vX) with step eta (Korpelevich).
@@ -425,6 +503,7 @@ kot_status run(kot_ctx* C, const std::function<void()>& body) {
     explicit Install(kot_ctx* c) { set_current_profiler(c && c->prof.mask ? &c->prof : nullptr); }
     ~Install() { set_current_profiler(nullptr); }
   } install(C);
+  if (C) C->force64 = false;
   try {
     body();
     return KOT_OK;
@@ -455,7 +534,7 @@ kot_status kot_create(kot_ctx** out, const kot_options* opt) {
   if (o.max_iter < 0 || o.cg_max_iter < 0 || !(o.tau > 0 && o.tau < 1) || !(o.kappa > 0) ||
       !(o.alpha1 > 0) || !(o.alpha2 >= o.alpha1) || !(o.beta0 > 0) || !(o.beta1 > 0) ||
       !(o.beta2 > 0) || !(o.theta0 > 0) || !(o.theta_min > 0) || !(o.theta_max >= o.theta_min) ||
-      !(o.jitter >= 0) || !(o.jitter_max >= o.jitter) ||
+      !(o.jitter >= 0) || !(o.jitter_max >= o.jitter) || o.eig_ctas < 0 || !(o.mixed_switch >= 0) ||
       (o.precision != KOT_FP64 && o.precision != KOT_MIXED))
     return KOT_ERR_INVALID;
   int ndev = 0;
@@ -496,6 +575,11 @@ kot_status kot_destroy(kot_ctx* C) {
                             &C->rt.r1, &C->rt.r2, &C->jw.A, &C->jw.V, &C->jw.rot, &C->jw.partial,
                             &C->jw.scal})
     b->release();
+  C->jw.bar.release();
+  C->jw.flags.release();
+  C->tc.a.release();
+  C->tc.b.release();
+  C->tc.err.release();
   for (auto& b : C->stage) b.release();
   for (EigSlot* e : {&C->ew, &C->ev, &C->et, &C->e1, &C->e2}) {
     e->P.release();
@@ -663,7 +747,7 @@ kot_status kot_newton_direction(kot_ctx* C, const double* gamma, const double* X
     const double* dg = dev_in(C, 0, gamma, l);
     const double* dXm = dev_in(C, 1, X, L2);
     residual(C, dg, dXm, C->ew, nullptr, C->rw);
-    const int it = newton_direction(C, C->rw, C->ew, mu, cg_tol_abs, C->dg.p, C->dX.p);
+    const int it = newton_direction(C, C->rw, C->ew, mu, cg_tol_abs, C->dg.p, C->dX.p, true);
     dev_out(C, dgamma, C->dg.p, l);
     dev_out(C, dX, C->dX.p, L2);
     KOT_CUDA(cudaStreamSynchronize(C->st));
@@ -692,6 +776,7 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
     cudaStream_t st = C->st;
     const kot_options& o = C->opt;
     reset_slots(C);
+    C->eig_calls = C->eig_sweeps = 0;
     if (gamma0) {
       const double* p = dev_in(C, 0, gamma0, l);
       KOT_CUDA(cudaMemcpyAsync(C->g.p, p, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -718,7 +803,9 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
         residual(C, C->vg.p, C->vX.p, C->ev, &C->ev, C->rv);
       }
       const double mu = theta * C->rw.norm;
-      cgt += newton_direction(C, C->rw, C->ew, mu, 0.0, C->dg.p, C->dX.p);
+      // mixed form: tensor-core products far from the solution, FP64 near it
+      cgt += newton_direction(C, C->rw, C->ew, mu, 0.0, C->dg.p, C->dX.p,
+                              C->rw.norm > o.mixed_switch);
       axpby(st, l, 1.0, C->g.p, 1.0, C->dg.p, C->tg.p);
       axpby(st, L2, 1.0, C->X.p, 1.0, C->dX.p, C->tX.p);
       residual(C, C->tg.p, C->tX.p, C->et, &C->ew, C->rt);
@@ -765,6 +852,8 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
     R.objective = obj;
     R.ot_hat = ot;
     R.eps = C->eps;
+    R.eig_calls = (int)C->eig_calls;
+    R.eig_sweeps = (int)C->eig_sweeps;
   });
   if (s == KOT_OK && !converged) {
     s = KOT_ERR_NO_CONVERGENCE;
@@ -774,6 +863,34 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
   R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (res) *res = R;
   return s;
+}
+
+kot_status kot_dense_product(kot_ctx* C, int M, int N, int K, double alpha, const double* A,
+                             int lda, int transA, const double* B, int ldb, int transB,
+                             double beta, double* Cm, int ldc, int pieces) {
+  if (!C) return KOT_ERR_INVALID;
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !Cm || pieces < 1 || pieces > 3 ||
+      lda < (transA ? M : K) || ldb < (transB ? N : K) || ldc < N || !std::isfinite(alpha) ||
+      !std::isfinite(beta)) {
+    C->err = "kot_dense_product: invalid argument";
+    return KOT_ERR_INVALID;
+  }
+  return run(C, [&] {
+    KOT_CUDA(cudaSetDevice(C->opt.device));
+    const size_t na = (size_t)(transA ? K : M) * lda, nb = (size_t)(transB ? K : N) * ldb;
+    const double* dA = dev_in(C, 0, A, na);
+    const double* dB = dev_in(C, 1, B, nb);
+    double* dC = Cm;
+    if (C->opt.host_pointers) {
+      C->stage[2].alloc((size_t)M * ldc);
+      KOT_CUDA(cudaMemcpyAsync(C->stage[2].p, Cm, (size_t)M * ldc * sizeof(double), cudaMemcpyHostToDevice, C->st));
+      dC = C->stage[2].p;
+    }
+    gemm_tc(C->st, C->tc, M, N, K, TcOperand{dA, lda, transA != 0, nullptr},
+            TcOperand{dB, ldb, transB != 0, nullptr}, pieces, alpha, beta, dC, ldc);
+    if (C->opt.host_pointers) dev_out(C, Cm, dC, (size_t)M * ldc);
+    if (gemm_tc_error(C->st, C->tc)) fail(KOT_ERR_TIMEOUT, "tensor-core GEMM wait timed out");
+  });
 }
 
 kot_status kot_launch_count(long long* out) {

@@ -39,13 +39,14 @@ long long launch_total();
 // Kernel classes the profiler can time (kot_kernel_class in kot.h uses the same numbering).
 enum KClass : int {
   KC_GEMM_F64 = 0,      // k_gemm_f64
-  KC_JACOBI_ROTATE = 1, // k_rotate (one Jacobi round)
-  KC_JACOBI_ANGLES = 2, // k_angles
+  KC_JACOBI = 1,        // k_jacobi_coop (all sweeps of one decomposition, FP64)
+  KC_JACOBI_F32 = 2,    // k_jacobi_coop<float> (mixed precision)
   KC_EMBED = 3,         // k_embed
   KC_PAIRS = 4,         // k_pair_tiles
   KC_GRAM = 5,          // k_gram
   KC_CHOL = 6,          // Cholesky diagonal / panel kernels
-  KC_COUNT = 7
+  KC_GEMM_TC = 7,       // k_tc_gemm_bf16 (tcgen05 tensor-core GEMM)
+  KC_COUNT = 8
 };
 
 // When a profiler is installed for the calling thread, instrumented launch sites record a CUDA
@@ -166,19 +167,42 @@ void rowsum_bounds(cudaStream_t st, int l, const double* Q, const double* Kt, do
 
 // ------------------------------------------------------------------ eigen (eig.cu)
 struct JacobiWork {
-  DevBuf<double> A, V;      // lp x lp
-  DevBuf<double> rot;       // lp/2 pairs * 2 (c, s)
+  DevBuf<double> A, V;      // A: two lp x lp buffers; V: lp x lp
+  DevBuf<double> rot;       // two rounds x lp/2 pairs x (c, s)
   DevBuf<int> pairs;        // lp
   DevBuf<int> rank;         // l
   DevBuf<double> partial, scal;
+  DevBuf<unsigned> bar;     // grid barrier [arrivals, generation]
+  DevBuf<int> flags;        // [error, 2 * sweeps + final buffer]
 };
 
 // Symmetric eigen-decomposition Z = P diag(sig) P^T, sig ascending.  Z: l x l (full
 // symmetric, read only).  If warm != nullptr its columns (an orthogonal l x l basis, row-major)
 // are used as the starting basis.  P: l x l output (row-major, column j = eigenvector j).
 // Returns the number of sweeps taken; throws on non-convergence within max_sweeps.
+// ctas: CTAs of the cooperative launch (0 = one per SM).
 int eig_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, double* P,
-                double* sig, JacobiWork& w, int max_sweeps, double* host_scal);
+                double* sig, JacobiWork& w, int max_sweeps, double* host_scal, int ctas);
+
+// ------------------------------------------------------------------ tensor cores (tc_gemm.cu)
+// Logical operand of C = alpha op(A) op(B)^T + beta C: element (r, k) is
+// (trans ? src[k * ld + r] : src[r * ld + k]) * (scale ? scale[k] : 1).
+struct TcOperand {
+  const double* src;
+  int ld;
+  bool trans;
+  const double* scale;
+};
+struct TcWork {
+  DevBuf<unsigned short> a, b;   // BF16 split operands
+  DevBuf<int> err;               // set by a CTA whose bounded wait gave up
+};
+// C (M x N, FP64, ldc) = alpha * sum_k opA(r=m, k) opB(r=n, k) + beta * C with K-length rows,
+// on tcgen05 tensor cores with each operand split into `pieces` BF16 terms (1..3).
+void gemm_tc(cudaStream_t st, TcWork& w, int M, int N, int K, const TcOperand& A,
+             const TcOperand& B, int pieces, double alpha, double beta, double* C, int ldc);
+// Nonzero if a tensor-core GEMM CTA timed out since the last call (clears the flag).
+int gemm_tc_error(cudaStream_t st, TcWork& w);
 
 // ------------------------------------------------------------------ Newton pieces (newton.cu)
 // Scale rows of V (na x l) for the G + G^T form of T: columns in alpha by 1/(2 mu), columns in

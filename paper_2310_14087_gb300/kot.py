@@ -32,14 +32,16 @@ class Options(C.Structure):
                 ("alpha2", C.c_double), ("beta0", C.c_double), ("beta1", C.c_double),
                 ("beta2", C.c_double), ("theta0", C.c_double), ("theta_min", C.c_double),
                 ("theta_max", C.c_double), ("eg_step", C.c_double), ("jitter", C.c_double),
-                ("jitter_max", C.c_double), ("use_eg", C.c_int), ("record_history", C.c_int)]
+                ("jitter_max", C.c_double), ("use_eg", C.c_int), ("record_history", C.c_int),
+                ("eig_ctas", C.c_int), ("mixed_switch", C.c_double)]
 
 
 class Result(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("ssn_accepted", C.c_int),
                 ("eg_taken", C.c_int), ("cg_total", C.c_int), ("residual", C.c_double),
                 ("r1_norm", C.c_double), ("r2_norm", C.c_double), ("objective", C.c_double),
-                ("ot_hat", C.c_double), ("eps", C.c_double), ("seconds", C.c_double)]
+                ("ot_hat", C.c_double), ("eps", C.c_double), ("seconds", C.c_double),
+                ("eig_calls", C.c_int), ("eig_sweeps", C.c_int)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -56,10 +58,10 @@ EXPORTS = ["kot_default_options", "kot_create", "kot_destroy", "kot_last_error",
            "kot_build_features", "kot_set_features", "kot_get_features", "kot_residual",
            "kot_newton_direction", "kot_ssn_solve", "kot_get_history", "kot_batch_solve",
            "kot_profile", "kot_profile_read", "kot_launch_count",
-           "kot_embedding_sqnorm_noalloc"]
+           "kot_embedding_sqnorm_noalloc", "kot_dense_product"]
 
-KERNEL_CLASSES = ["gemm_f64", "jacobi_rotate", "jacobi_angles", "embed", "pair_sums", "gram",
-                  "cholesky"]
+KERNEL_CLASSES = ["gemm_f64", "jacobi_f64", "jacobi_f32", "embed", "pair_sums", "gram",
+                  "cholesky", "gemm_tc"]
 
 
 class KernelStats(C.Structure):
@@ -94,6 +96,7 @@ def lib() -> C.CDLL:
         "kot_profile": (i, [vp, i]),
         "kot_profile_read": (i, [vp, i, C.POINTER(KernelStats)]),
         "kot_launch_count": (i, [C.POINTER(C.c_longlong)]),
+        "kot_dense_product": (i, [vp, i, i, i, d, vp, i, i, vp, i, i, d, vp, i, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -211,6 +214,12 @@ class Context:
         self._check(lib().kot_ssn_solve(self.h, tol, _ptr(gamma_out), _ptr(X_out), _ptr(gamma0),
                                         _ptr(X0), C.byref(r)), ok)
         return r
+
+    def dense_product(self, M, N, K, alpha, A, lda, transA, B, ldb, transB, beta, Cm, ldc,
+                      pieces=3):
+        return self._check(lib().kot_dense_product(self.h, M, N, K, alpha, _ptr(A), lda, transA,
+                                                   _ptr(B), ldb, transB, beta, _ptr(Cm), ldc,
+                                                   pieces))
 
     def profile(self, mask: int):
         return self._check(lib().kot_profile(self.h, mask))

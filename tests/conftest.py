@@ -1,6 +1,11 @@
 import os
 import sys
 
+# single-threaded BLAS: the oracle's Algorithm 2 trajectory depends on rounding, and threaded
+# reductions would make it differ from run to run
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))

@@ -9,7 +9,7 @@ from __future__ import annotations
 import numpy as np
 
 
-def ipm_solve(Q, z, q2, R, lambda1, lambda2, t_end=1e-11):
+def ipm_solve(Q, z, q2, R, lambda1, lambda2, t_end=1e-13):
     """Damped-Newton log-barrier method for
         min  gamma^T Q gamma/(4 l2) - gamma^T z/(2 l2) + q2/(4 l2)
         s.t. R diag(gamma) R^T + lambda1 I >= 0.
