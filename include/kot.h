@@ -67,8 +67,11 @@ typedef struct {
   int use_eg;              /* 1: Algorithm 2 with the EG safeguard; 0: plain SSN steps   */
   int record_history;      /* 1: keep ||R(w_k)|| per iteration (kot_get_history)         */
   int eig_ctas;            /* CTAs of the cooperative Jacobi eigensolver; 0 = one per SM  */
-  double mixed_switch;     /* mixed form: tensor-core Newton directions while ||R(w_k)|| > this;
-                              FP64 directions below it (default 1e-4)                     */
+  double mixed_switch;     /* mixed form: tensor-core CG for the Newton direction while
+                              ||R(w_k)|| > this (its result is always re-checked against
+                              Eq. (4.3) in FP64 and finished in FP64 if short), plain FP64
+                              CG below it (default 1e-4)                                   */
+  int batch_workers;       /* kot_batch_solve: problems solved concurrently (0 = 4)        */
 } kot_options;
 
 typedef struct {
@@ -149,6 +152,13 @@ kot_status kot_ssn_solve(kot_ctx* ctx, double tol, double* gamma_out, double* X_
  * of ||R(w_k)|| to the host array hist; *count receives the number copied. */
 kot_status kot_get_history(kot_ctx* ctx, double* hist, int cap, int* count);
 
+/* Per-iteration trace of the last solve (record_history = 1): up to cap rows of five doubles
+ * {||R(w_{k+1})||, mu_k, CG steps, theta_{k+1}, direction kind (0 FP64 products, 1 tensor-core
+ * products that passed the FP64 check of Eq. (4.3) as they were, 2 tensor-core products plus
+ * FP64 CG steps)} into the host array out (5 * cap doubles);
+ * *count receives the number of rows. */
+kot_status kot_get_trace(kot_ctx* ctx, double* out, int cap, int* count);
+
 /* One problem of a batch.  Arrays follow the context's pointer mode. */
 typedef struct {
   int d, n, l;
@@ -158,8 +168,10 @@ typedef struct {
 } kot_problem;
 
 /* Solve B independent problems (features + Algorithm 2 each).  res receives B results (host
- * array).  Problems are run largest-first on the context's device.  The call returns the first
- * non-OK status among the problems (KOT_OK if all converged); each res[i].status is per problem. */
+ * array).  Problems are handed out largest-first to batch_workers concurrent worker contexts
+ * (each with its own stream and buffers, driven by its own host thread; their eigensolver
+ * launches share the SMs) on the context's device.  The call returns the first non-OK status
+ * in problem order (KOT_OK if all converged); each res[i].status is per problem. */
 kot_status kot_batch_solve(kot_ctx* ctx, int B, const kot_problem* probs, kot_result* res);
 
 /* ---- building block of the mixed form: dense product on the tensor cores ----

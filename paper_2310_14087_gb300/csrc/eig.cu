@@ -102,10 +102,12 @@ __device__ __forceinline__ unsigned atom_add_acqrel_u32(unsigned* p, unsigned v)
 }
 
 // Grid-wide barrier for a cooperative launch.  bar[0] counts arrivals and bar[1] holds the last
-// completed epoch; both are zeroed by the host before the launch and only grow, so no reset
-// races.  Arrival is one acquire-release atomic per CTA (it publishes the CTA's writes, ordered
-// before it by __syncthreads, and the last arriver, which sees count == epoch * nblocks,
-// publishes the epoch with a release store).  Returns false (and sets *err) if the wait gave up.
+// completed epoch; both are zeroed by the host before the launch and only grow, so there is no
+// reset race.  Arrival is one acquire-release atomic per CTA (it publishes the CTA's writes,
+// ordered before it by __syncthreads); the last arriver, which sees count == epoch * nblocks,
+// publishes the epoch with one release store.  (Measured on GB300 at 152 CTAs: ~2.4 us; one
+// release store per CTA flag costs ~50 us, a fence plus relaxed per-CTA stores ~3.1 us.)
+// Returns false (and sets *err) if the wait gave up.
 __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned& epoch, int* err) {
   __shared__ int ok;
   __syncthreads();
@@ -147,18 +149,33 @@ struct CoopArgs {
   double floor_rel;    // ... or when a sweep stalls (off > 0.5 prev) below floor_rel * ||A||_F
 };
 
+// Jacobi rotation (c, s) for the pair (p, q): the 2 x 2 symmetric Schur step.  The angle is
+// computed in FP32 -- from the FP64 difference a_qq - a_pp, so nearly equal diagonal entries do
+// not cancel -- which is ~10x shorter than the FP64 divide/square-root chain on this part; the
+// pair (c, s) is then renormalised in FP64 (two Newton steps on c^2 + s^2 = 1), so every rotation
+// is orthogonal to FP64 precision and A stays an exact similarity transform of Z.  The rotated
+// entry is left at ~1e-7 |a_pq| instead of 0 and is removed by the next sweep.
 template <typename T>
 __device__ __forceinline__ void rot_angle(T app, T aqq, T apq, T& c, T& s) {
   c = T(1);
   s = T(0);
-  if (apq != T(0)) {
-    const T tau = (aqq - app) / (T(2) * apq);
-    T t;
-    if (fabs((double)tau) > 1e150) t = T(0.5) / tau;
-    else t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
-    c = T(1) / sqrt(T(1) + t * t);
-    s = t * c;
+  const float fpq = (float)apq;
+  const float fd = (float)(aqq - app);
+  if (fpq == 0.0f || !(fabsf(fpq) > 1e-30f * fabsf(fd))) return;
+  const float tau = fd / (2.0f * fpq);
+  float t;
+  if (fabsf(tau) > 1e18f) t = 0.5f / tau;
+  else t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+  const float fc = rsqrtf(1.0f + t * t);
+  T c0 = (T)fc, s0 = (T)(t * fc);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {   // Newton steps on c^2 + s^2 = 1: 1e-7 -> 1e-14 -> rounding
+    const T corr = T(1.5) - T(0.5) * (c0 * c0 + s0 * s0);
+    c0 *= corr;
+    s0 *= corr;
   }
+  c = c0;
+  s = s0;
 }
 
 // New 2x2 block J_a^T M J_b (rows p_a, q_a; columns p_b, q_b).
@@ -273,7 +290,11 @@ __global__ void __launch_bounds__(kCoopThreads) k_jacobi_coop(CoopArgs<T> a) {
       T* rn = rot[(gr + 1) & 1];
       const int rnext = (r + 1 == lp - 1) ? 0 : r + 1;
       const int nA = half * half, nV = l * half, nN = half;
-      for (int it = (int)gtid; it < nA + nV + nN; it += (int)gstride) {
+      // next-round angle items are dealt round-robin over the CTAs (item k -> CTA k mod grid,
+      // thread k / grid): a few FP64 divide/square-root chains per SM instead of all of them on
+      // the one or two SMs a contiguous range would land on (FP64 issues ~2 ops/clk per SM)
+      for (int it0 = (int)(threadIdx.x * nb + blockIdx.x); it0 < nA + nV + nN; it0 += (int)gstride) {
+        const int it = (it0 < nN) ? nA + nV + it0 : it0 - nN;
         if (it < nA) {
           const int ia = it / half, ib = it - ia * half;
           if (ib < ia) continue;
@@ -289,8 +310,8 @@ __global__ void __launch_bounds__(kCoopThreads) k_jacobi_coop(CoopArgs<T> a) {
           if (ia == ib) {
             dst[(size_t)pa * lp + pa] = n00;
             dst[(size_t)qa * lp + qa] = n11;
-            dst[(size_t)pa * lp + qa] = T(0);
-            dst[(size_t)qa * lp + pa] = T(0);
+            dst[(size_t)pa * lp + qa] = n01;
+            dst[(size_t)qa * lp + pa] = n01;
           } else {
             dst[(size_t)pa * lp + pb] = n00;
             dst[(size_t)pa * lp + qb] = n01;
@@ -333,7 +354,7 @@ __global__ void __launch_bounds__(kCoopThreads) k_jacobi_coop(CoopArgs<T> a) {
           aqq = (qn == pq_) ? d00 : d11;
           // off-diagonal entry (pn, qn): block (slot sp rows) x (slot sq columns)
           if (sp == sq) {
-            apq = T(0);
+            apq = d01;   // never happens for round-robin pairings (consecutive rounds differ)
           } else {
             rot_block<T>(cp, spn, cq, sqn, __ldcg(src + (size_t)pp * lp + pq_), __ldcg(src + (size_t)pp * lp + qq),
                          __ldcg(src + (size_t)qp * lp + pq_), __ldcg(src + (size_t)qp * lp + qq), d00, d01, d10, d11);

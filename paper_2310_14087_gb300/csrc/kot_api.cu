@@ -7,7 +7,9 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <atomic>
 #include <numeric>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -67,6 +69,8 @@ struct kot_ctx {
   bool force64 = false;   // mixed form: run the Newton-direction products in FP64 for now
   long long eig_calls = 0, eig_sweeps = 0;
   std::vector<double> hist;
+  std::vector<double> trace;   // per iteration: ||R||, mu, CG steps, theta, direction kind
+  int last_dir_kind = 0;       // 0 FP64, 1 tensor cores, 2 tensor cores + FP64 refinement
   Profiler prof;
 };
 
@@ -99,6 +103,7 @@ void set_defaults(kot_options* o) {
   o->record_history = 0;
   o->eig_ctas = 0;
   o->mixed_switch = 1e-4;
+  o->batch_workers = 0;
 }
 
 bool pos_finite(double v) { return std::isfinite(v) && v > 0.0; }
@@ -297,11 +302,13 @@ void t_apply(kot_ctx* C, const EigSlot& e, double mu, const double* S, double* o
 }
 
 // Algorithm 1 at w (residual r, eigen-decomposition e).  Returns CG iterations.
-// Mixed form: the products run on the tensor cores; if CG reaches its cap without meeting the
-// test of Eq. (4.3) (the products' ~1e-7 error times the Schur system's condition ~1/mu leaves
-// it short near the solution), the direction is refined in FP64: the right-hand side is
+// Mixed form: CG runs with tensor-core products first.  Its recursive residual belongs to the
+// inexact operator, so the test of Eq. (4.3) is then re-taken in FP64: the right-hand side is
 // recomputed, the true residual a1 - H x of the mixed solution is formed, and CG continues from
-// that x with FP64 products for up to cg_max_iter more iterations.
+// that x with FP64 products (up to cg_max_iter more iterations) until the FP64 test holds.  The
+// returned direction therefore meets Eq. (4.3) as FP64 measures it; without this check the
+// directions' ~1e-7/mu error makes rho_k small once mu_k = theta_k ||r_k|| is small, the theta
+// rule multiplies theta by beta2, and convergence turns linear.
 int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu, double cg_tol_abs,
                      double* dgam, double* dX, bool allow_tc) {
   const int l = C->l;
@@ -317,13 +324,10 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
   double* Hp = C->v6.p;
   const int cap = cg_tol_abs > 0 ? 10 * l + 50 : C->opt.cg_max_iter;
   const bool refine = mixed(C);
-  int total = 0;
+  int total = 0, refined_steps = 0;
   bool met = false;
   for (int phase = 0; phase < (refine ? 2 : 1); ++phase) {
-    if (phase == 1) {
-      if (met) break;
-      C->force64 = true;
-    }
+    if (phase == 1) C->force64 = true;   // always verify a tensor-core direction in FP64
     // right-hand side: a1 = -r1 - Phi(r2 + T[r2])/(mu+1), at2 = -(r2 + T[r2])/(mu+1)
     t_apply(C, e, mu, r.r2.p, rT);
     axpby(st, L2, 1.0, r.r2.p, 1.0, rT, rT);
@@ -392,7 +396,10 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
       ++it;
     }
     total += it;
+    if (phase == 1) refined_steps = it;
   }
+  // 1: tensor-core direction accepted by the FP64 check as is; 2: FP64 steps were added
+  C->last_dir_kind = refine ? (refined_steps == 0 ? 1 : 2) : 0;
   C->force64 = false;
   axpby(st, L2, 1.0, at2, -1.0, TPx, dX);
   if (C->opt.precision == KOT_MIXED && gemm_tc_error(st, C->tc))
@@ -534,7 +541,7 @@ kot_status kot_create(kot_ctx** out, const kot_options* opt) {
   if (o.max_iter < 0 || o.cg_max_iter < 0 || !(o.tau > 0 && o.tau < 1) || !(o.kappa > 0) ||
       !(o.alpha1 > 0) || !(o.alpha2 >= o.alpha1) || !(o.beta0 > 0) || !(o.beta1 > 0) ||
       !(o.beta2 > 0) || !(o.theta0 > 0) || !(o.theta_min > 0) || !(o.theta_max >= o.theta_min) ||
-      !(o.jitter >= 0) || !(o.jitter_max >= o.jitter) || o.eig_ctas < 0 || !(o.mixed_switch >= 0) ||
+      !(o.jitter >= 0) || !(o.jitter_max >= o.jitter) || o.eig_ctas < 0 || !(o.mixed_switch >= 0) || o.batch_workers < 0 ||
       (o.precision != KOT_FP64 && o.precision != KOT_MIXED))
     return KOT_ERR_INVALID;
   int ndev = 0;
@@ -795,6 +802,7 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
     const double eta = o.eg_step > 0 ? o.eg_step : 1.0 / C->eg_L;
     residual(C, C->g.p, C->X.p, C->ew, nullptr, C->rw);
     C->hist.clear();
+    C->trace.clear();
     if (o.record_history) C->hist.push_back(C->rw.norm);
     int it = 0, acc = 0, egt = 0, cgt = 0;
     while (C->rw.norm > tol && it < o.max_iter) {
@@ -804,8 +812,9 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
       }
       const double mu = theta * C->rw.norm;
       // mixed form: tensor-core products far from the solution, FP64 near it
-      cgt += newton_direction(C, C->rw, C->ew, mu, 0.0, C->dg.p, C->dX.p,
-                              C->rw.norm > o.mixed_switch);
+      const int cgk = newton_direction(C, C->rw, C->ew, mu, 0.0, C->dg.p, C->dX.p,
+                                       C->rw.norm > o.mixed_switch);
+      cgt += cgk;
       axpby(st, l, 1.0, C->g.p, 1.0, C->dg.p, C->tg.p);
       axpby(st, L2, 1.0, C->X.p, 1.0, C->dX.p, C->tX.p);
       residual(C, C->tg.p, C->tX.p, C->et, &C->ew, C->rt);
@@ -834,7 +843,10 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
         ++egt;
       }
       ++it;
-      if (o.record_history) C->hist.push_back(C->rw.norm);
+      if (o.record_history) {
+        C->hist.push_back(C->rw.norm);
+        for (double v : {C->rw.norm, mu, (double)cgk, theta, (double)C->last_dir_kind}) C->trace.push_back(v);
+      }
     }
     converged = C->rw.norm <= tol;
     double ot = 0;
@@ -919,6 +931,14 @@ kot_status kot_profile_read(kot_ctx* C, int cls, kot_kernel_stats* out) {
   });
 }
 
+kot_status kot_get_trace(kot_ctx* C, double* out, int cap, int* count) {
+  if (!C || !out || cap < 0 || !count) return KOT_ERR_INVALID;
+  const int rows = std::min<int>(cap, (int)(C->trace.size() / 5));
+  std::copy(C->trace.begin(), C->trace.begin() + 5 * rows, out);
+  *count = rows;
+  return KOT_OK;
+}
+
 kot_status kot_get_history(kot_ctx* C, double* hist, int cap, int* count) {
   if (!C || !hist || cap < 0 || !count) return KOT_ERR_INVALID;
   const int m = std::min<int>(cap, (int)C->hist.size());
@@ -942,22 +962,54 @@ kot_status kot_batch_solve(kot_ctx* C, int B, const kot_problem* probs, kot_resu
       return KOT_ERR_INVALID;
     }
   }
-  // largest problems first (cost grows like l^3)
+  if (B == 0) return KOT_OK;
+  // largest problems first (cost grows like l^3), handed out through a shared counter
   std::vector<int> order(B);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return probs[a].l > probs[b].l; });
-  kot_status first = KOT_OK;
-  for (int i : order) {
-    const kot_problem& p = probs[i];
-    kot_status s = kot_build_features(C, p.d, p.n, p.X, p.Y, p.l, p.Xf, p.Yf, p.sigma, p.lambda1,
-                                      p.lambda2);
-    if (s == KOT_OK) s = kot_ssn_solve(C, p.tol, p.gamma_out, nullptr, nullptr, nullptr, &res[i]);
-    else {
-      res[i] = kot_result{};
-      res[i].status = s;
+  // Each problem is latency-bound on its own, so several run at once: W worker contexts, each
+  // with its own stream and buffers, driven by one host thread each; their cooperative
+  // eigensolver launches take a share of the SMs so that all of them fit at the same time.
+  int W = C->opt.batch_workers > 0 ? C->opt.batch_workers : 4;
+  W = std::max(1, std::min(W, B));
+  int nsm = 152;
+  cudaSetDevice(C->opt.device);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, C->opt.device);
+  std::vector<kot_ctx*> workers(W, nullptr);
+  for (int w = 0; w < W; ++w) {
+    kot_options o = C->opt;
+    o.stream = nullptr;
+    o.batch_workers = 1;
+    if (o.eig_ctas == 0) o.eig_ctas = std::max(8, nsm / W);
+    kot_status s = kot_create(&workers[w], &o);
+    if (s != KOT_OK) {
+      for (kot_ctx* x : workers) kot_destroy(x);
+      C->err = "kot_batch_solve: could not create worker contexts";
+      return s;
     }
-    if (s != KOT_OK && first == KOT_OK) first = s;
   }
+  std::atomic<int> next{0};
+  auto work = [&](kot_ctx* X) {
+    for (int k = next.fetch_add(1); k < B; k = next.fetch_add(1)) {
+      const int i = order[k];
+      const kot_problem& p = probs[i];
+      kot_status s = kot_build_features(X, p.d, p.n, p.X, p.Y, p.l, p.Xf, p.Yf, p.sigma, p.lambda1,
+                                        p.lambda2);
+      if (s == KOT_OK) s = kot_ssn_solve(X, p.tol, p.gamma_out, nullptr, nullptr, nullptr, &res[i]);
+      else {
+        res[i] = kot_result{};
+        res[i].status = s;
+      }
+    }
+  };
+  std::vector<std::thread> threads;
+  for (int w = 1; w < W; ++w) threads.emplace_back(work, workers[w]);
+  work(workers[0]);
+  for (auto& t : threads) t.join();
+  for (kot_ctx* x : workers) kot_destroy(x);
+  kot_status first = KOT_OK;
+  for (int i = 0; i < B && first == KOT_OK; ++i)
+    if (res[i].status != KOT_OK) first = (kot_status)res[i].status;
   return first;
 }
 

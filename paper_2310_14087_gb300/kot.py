@@ -33,7 +33,8 @@ class Options(C.Structure):
                 ("beta2", C.c_double), ("theta0", C.c_double), ("theta_min", C.c_double),
                 ("theta_max", C.c_double), ("eg_step", C.c_double), ("jitter", C.c_double),
                 ("jitter_max", C.c_double), ("use_eg", C.c_int), ("record_history", C.c_int),
-                ("eig_ctas", C.c_int), ("mixed_switch", C.c_double)]
+                ("eig_ctas", C.c_int), ("mixed_switch", C.c_double),
+                ("batch_workers", C.c_int)]
 
 
 class Result(C.Structure):
@@ -58,7 +59,7 @@ EXPORTS = ["kot_default_options", "kot_create", "kot_destroy", "kot_last_error",
            "kot_build_features", "kot_set_features", "kot_get_features", "kot_residual",
            "kot_newton_direction", "kot_ssn_solve", "kot_get_history", "kot_batch_solve",
            "kot_profile", "kot_profile_read", "kot_launch_count",
-           "kot_embedding_sqnorm_noalloc", "kot_dense_product"]
+           "kot_embedding_sqnorm_noalloc", "kot_dense_product", "kot_get_trace"]
 
 KERNEL_CLASSES = ["gemm_f64", "jacobi_f64", "jacobi_f32", "embed", "pair_sums", "gram",
                   "cholesky", "gemm_tc"]
@@ -97,6 +98,7 @@ def lib() -> C.CDLL:
         "kot_profile_read": (i, [vp, i, C.POINTER(KernelStats)]),
         "kot_launch_count": (i, [C.POINTER(C.c_longlong)]),
         "kot_dense_product": (i, [vp, i, i, i, d, vp, i, i, vp, i, i, d, vp, i, i]),
+        "kot_get_trace": (i, [vp, vp, i, C.POINTER(i)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -228,6 +230,13 @@ class Context:
         st = KernelStats()
         self._check(lib().kot_profile_read(self.h, cls, C.byref(st)))
         return st
+
+    def trace(self, cap=100000) -> np.ndarray:
+        """Per-iteration rows (||R||, mu, CG steps, theta, direction kind) of the last solve."""
+        buf = np.zeros(5 * cap)
+        cnt = C.c_int(0)
+        self._check(lib().kot_get_trace(self.h, buf.ctypes.data, cap, C.byref(cnt)))
+        return buf[:5 * cnt.value].reshape(-1, 5).copy()
 
     def history(self, cap=100000) -> np.ndarray:
         buf = np.zeros(cap)

@@ -185,6 +185,19 @@ def paper_regime(seed: int = 0, d: int = 5, n: int = 1000, l: int = 300,
                    Fp[:, d:].copy(), float(np.sqrt(sigma2)), 1.0 / l, 1.0 / np.sqrt(n))
 
 
+def paper_regime_batch(count: int = 256, base_seed: int = 5000, l_max: int = 512) -> list[Problem]:
+    """Uneven batch in the Sec. 5 regime with the size ranges of the batched configuration:
+    d ~ U{2..20}, n ~ U[200, 2000], l ~ U[32, l_max]; problem b is paper_regime(seed base+b)."""
+    out = []
+    for b in range(count):
+        rng = np.random.default_rng(base_seed + b)
+        d = int(rng.integers(2, 21))
+        n = int(rng.integers(200, 2001))
+        l = int(rng.integers(32, l_max + 1))
+        out.append(paper_regime(seed=base_seed + b, d=d, n=n, l=l, name=f"paper_batch_{b}"))
+    return out
+
+
 def by_name(name: str) -> Problem:
     """Named workloads: 'd2_n100_l50', 'd5_n1000_l300', 'd10_n2000_l1024', 'd64_n4000_l2048'."""
     table = {

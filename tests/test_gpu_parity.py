@@ -311,8 +311,10 @@ def test_mixed_solve_gates(name):
     ctx = kot.Context(device=0, precision=kot.MIXED)
     ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
     g, X = Z(p.l), Z(p.l, p.l)
+    ctx.profile(1 << kot.KERNEL_CLASSES.index("gemm_tc"))
     res = ctx.ssn_solve(p.tol, g, X)
     assert res.status == kot.OK
+    assert ctx.profile_read(kot.KERNEL_CLASSES.index("gemm_tc")).launches > 0   # tensor cores ran
     check = ko.residual(F, N(g), N(X))
     assert check.norm <= p.tol * (1 + 1e-6)          # the oracle confirms the stopping test
     fstar, gstar = _optimum(F)
