@@ -72,6 +72,9 @@ typedef struct {
                               Eq. (4.3) in FP64 and finished in FP64 if short), plain FP64
                               CG below it (default 1e-4)                                   */
   int batch_workers;       /* kot_batch_solve: problems solved concurrently (0 = 4)        */
+  int eig_refine;          /* eigen-decompositions with a warm basis (the previous one of the
+                              same sequence): at most this many refinement steps from it
+                              before falling back to Jacobi sweeps; 0 = always Jacobi (default 5) */
 } kot_options;
 
 typedef struct {
@@ -85,6 +88,8 @@ typedef struct {
   double seconds;          /* wall time of the call                                      */
   int eig_calls;           /* symmetric eigen-decompositions performed by the solve      */
   int eig_sweeps;          /* Jacobi sweeps summed over them                             */
+  int eig_refined;         /* decompositions finished by refining the warm basis         */
+  int eig_refine_steps;    /* refinement steps summed over them                          */
 } kot_result;
 
 /* Fill *opt with the defaults listed above.  Returns KOT_ERR_INVALID if opt is NULL. */
@@ -173,6 +178,21 @@ typedef struct {
  * launches share the SMs) on the context's device.  The call returns the first non-OK status
  * in problem order (KOT_OK if all converged); each res[i].status is per problem. */
 kot_status kot_batch_solve(kot_ctx* ctx, int B, const kot_problem* probs, kot_result* res);
+
+/* ---- building block: symmetric eigen-decomposition (Sec. 4.1, Eq. (4.4)) ----
+ * The projection onto the PSD cone and the weights Omega of the generalized Jacobian are read
+ * off Z = P diag(sig) P^T.  Z: l x l, row-major, symmetric (the library uses (Z + Z^T)/2).
+ * P: l x l output, row-major, column j = eigenvector j; sig: l eigenvalues, ascending.
+ * warm (may be NULL): an orthogonal l x l basis (row-major, orthonormal columns) close to the
+ * eigenbasis, e.g. the one of a nearby matrix.  With it the library first refines warm into
+ * the eigenbasis (Ogita-Aishima iteration, at most opt.eig_refine steps of FP64 products) and
+ * rebuilds by Jacobi sweeps from warm when that does not converge; without it, Jacobi from the
+ * identity.  info (host, may be NULL) receives {Jacobi sweeps, refinement steps} of the call.
+ * Pointers follow the context's pointer mode.  No features are needed.  KOT_ERR_TIMEOUT if a
+ * bounded wait of the cooperative Jacobi kernel gave up, KOT_ERR_NO_CONVERGENCE if the sweeps
+ * did not converge. */
+kot_status kot_eig_sym(kot_ctx* ctx, int l, const double* Z, const double* warm, double* P,
+                       double* sig, int* info);
 
 /* ---- building block of the mixed form: dense product on the tensor cores ----
  * C = alpha * op(A) * op(B)^T + beta * C, C: M x N (ldc), op(A): M x K, op(B): N x K, where

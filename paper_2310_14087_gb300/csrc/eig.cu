@@ -12,6 +12,7 @@
 // the textbook 2 x 2 symmetric Schur step (Golub & Van Loan) that zeroes A_pq.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "kot_internal.cuh"
 
@@ -75,6 +76,84 @@ __global__ void k_gather(int l, int lp, const double* __restrict__ A, const doub
   const int rj = rank[j];
   P[(size_t)i * l + rj] = V[(size_t)i * lp + j];
   if (i == 0) sig[rj] = A[(size_t)j * lp + j];
+}
+
+// ------------------------------------------------------------------ refinement of a warm basis
+// One step of the iterative refinement of Ogita and Aishima (Japan J. Indust. Appl. Math. 35,
+// 2018) for an approximate eigenbasis X of Z.  Writing X = X*(I + D) with X* an exact eigenbasis,
+// G = X^T X ~ I + D + D^T and S = X^T Z X ~ L + D^T L + L D to first order, so
+//   lam_i = S_ii / G_ii,   E_ii = (1 - G_ii) / 2,   E_ij = (S_ij - lam_j G_ij) / (lam_j - lam_i)
+// gives E ~ -D and X (I + E) is an eigenbasis up to O(|D|^2): both the off-diagonal of the
+// rotated Z and the loss of orthogonality shrink quadratically.  This kernel writes F = I + E,
+// lam, and the largest |E_ij| (i != j) and |delta_ij - G_ij| as ordered bit patterns (a non-finite
+// E orders above every finite value, so it always reads as "not converged").
+__global__ void k_refine_correction(int l, const double* __restrict__ S, const double* __restrict__ G,
+                                    double* __restrict__ F, double* __restrict__ lam,
+                                    unsigned long long* __restrict__ mx) {
+  const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
+  double e_abs = 0.0, r_abs = 0.0;
+  if (i < l && j < l) {
+    const size_t ij = (size_t)i * l + j;
+    const double g = G[ij];
+    const double lj = S[(size_t)j * l + j] / G[(size_t)j * l + j];
+    double f;
+    if (i == j) {
+      f = 1.0 + 0.5 * (1.0 - g);
+      r_abs = fabs(1.0 - g);
+      lam[j] = lj;
+    } else {
+      const double li = S[(size_t)i * l + i] / G[(size_t)i * l + i];
+      f = (S[ij] - lj * g) / (lj - li);
+      e_abs = fabs(f);
+      r_abs = fabs(g);
+      if (!(e_abs <= 1e300)) e_abs = INFINITY;   // 0/0 or x/0: never converged
+    }
+    F[ij] = f;
+  }
+  // block maxima (non-negative doubles order like their bit patterns)
+  __shared__ unsigned long long sm[2][8];
+  unsigned long long be = (unsigned long long)__double_as_longlong(e_abs);
+  unsigned long long br = (unsigned long long)__double_as_longlong(r_abs);
+  for (int o = 16; o > 0; o >>= 1) {
+    be = max(be, __shfl_xor_sync(0xffffffffu, be, o));
+    br = max(br, __shfl_xor_sync(0xffffffffu, br, o));
+  }
+  if (threadIdx.x == 0) {
+    sm[0][threadIdx.y] = be;
+    sm[1][threadIdx.y] = br;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    for (int y = 1; y < 8; ++y) {
+      be = max(be, sm[0][y]);
+      br = max(br, sm[1][y]);
+    }
+    atomicMax(mx, be);
+    atomicMax(mx + 1, br);
+  }
+}
+
+// rank_j = #{ i : lam_i < lam_j or (lam_i == lam_j and i < j) }
+__global__ void k_rank_vec(int l, const double* __restrict__ lam, int* __restrict__ rank) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= l) return;
+  const double dj = lam[j];
+  int r = 0;
+  for (int i = 0; i < l; ++i) {
+    const double di = lam[i];
+    r += (di < dj) || (di == dj && i < j);
+  }
+  rank[j] = r;
+}
+
+__global__ void k_gather_vec(int l, const double* __restrict__ lam, const double* __restrict__ X,
+                             const int* __restrict__ rank, double* __restrict__ P,
+                             double* __restrict__ sig) {
+  const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
+  if (i >= l || j >= l) return;
+  const int rj = rank[j];
+  P[(size_t)i * l + rj] = X[(size_t)i * l + j];
+  if (i == 0) sig[rj] = lam[j];
 }
 
 
@@ -375,8 +454,80 @@ __global__ void __launch_bounds__(kCoopThreads) k_jacobi_coop(CoopArgs<T> a) {
 }
 }  // namespace
 
+int jacobi_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, double* P,
+                   double* sig, JacobiWork& w, int max_sweeps, double* host_scal, int ctas);
+
+namespace {
+
+// Refinement thresholds on max |E_ij|: above kRefineGiveUp the warm basis is too far for the
+// quadratic regime (or a pair is degenerate) and Jacobi takes over; at or below kRefineDone the
+// step just taken leaves an error of order kRefineDone^2 (below FP64 rounding), so it is the last.
+constexpr double kRefineGiveUp = 0.05;
+constexpr double kRefineDone = 1e-8;
+
+// Refine the warm basis into P, sig (ascending).  Returns the steps taken, or 0 if the iteration
+// gave up (P and sig are then untouched).
+int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, double* P,
+                   double* sig, JacobiWork& w, int max_steps) {
+  const size_t L2 = (size_t)l * l;
+  for (DevBuf<double>* b : {&w.Xa, &w.Xb, &w.Y, &w.S, &w.G, &w.F}) b->alloc(L2);
+  w.lam.alloc((size_t)l);
+  w.rank.alloc((size_t)l);
+  w.mx.alloc(2);
+  const dim3 g2(cdiv(l, 32), cdiv(l, 8)), b2(32, 8);
+  const double* X = warm;
+  for (int k = 0; k < max_steps; ++k) {
+    double* Xn = (k & 1) ? w.Xb.p : w.Xa.p;
+    gemm_f64(st, false, false, l, l, l, 1.0, Z, l, X, l, nullptr, 0.0, w.Y.p, l, 0);       // Y = Z X
+    gemm_f64(st, true, false, l, l, l, 1.0, X, l, w.Y.p, l, nullptr, 0.0, w.S.p, l, G_SYM); // S = X^T Y
+    gemm_f64(st, true, false, l, l, l, 1.0, X, l, X, l, nullptr, 0.0, w.G.p, l, G_SYM);     // G = X^T X
+    KOT_CUDA(cudaMemsetAsync(w.mx.p, 0, 2 * sizeof(unsigned long long), st));
+    {
+      ProfScope ps(st, KC_REFINE, 12.0 * (double)L2, 8.0 * 3.0 * (double)L2);
+      k_refine_correction<<<g2, b2, 0, st>>>(l, w.S.p, w.G.p, w.F.p, w.lam.p, w.mx.p);
+      KOT_CHECK_LAUNCH();
+      KOT_LAUNCHED(1);
+    }
+    gemm_f64(st, false, false, l, l, l, 1.0, X, l, w.F.p, l, nullptr, 0.0, Xn, l, 0);       // X (I + E)
+    unsigned long long hm[2] = {0, 0};
+    KOT_CUDA(cudaMemcpyAsync(hm, w.mx.p, sizeof(hm), cudaMemcpyDeviceToHost, st));
+    KOT_CUDA(cudaStreamSynchronize(st));
+    double me, mr;
+    std::memcpy(&me, &hm[0], sizeof(double));
+    std::memcpy(&mr, &hm[1], sizeof(double));
+    if (!(me <= kRefineGiveUp) || !(mr <= kRefineGiveUp)) return 0;
+    X = Xn;
+    if (me <= kRefineDone && mr <= kRefineDone) {
+      k_rank_vec<<<cdiv(l, 128), 128, 0, st>>>(l, w.lam.p, w.rank.p);
+      k_gather_vec<<<g2, b2, 0, st>>>(l, w.lam.p, X, w.rank.p, P, sig);
+      KOT_CHECK_LAUNCH();
+      KOT_LAUNCHED(2);
+      return k + 1;
+    }
+  }
+  return 0;
+}
+
+}  // namespace
+
 int eig_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, double* P,
-                double* sig, JacobiWork& w, int max_sweeps, double* host_scal, int ctas) {
+                double* sig, JacobiWork& w, int max_sweeps, double* host_scal, int ctas,
+                int max_refine) {
+  w.last_sweeps = 0;
+  w.last_refine = 0;
+  if (warm && max_refine > 0) {
+    const int k = refine_sym_f64(st, l, Z, warm, P, sig, w, max_refine);
+    if (k > 0) {
+      w.last_refine = k;
+      return 0;
+    }
+  }
+  w.last_sweeps = jacobi_sym_f64(st, l, Z, warm, P, sig, w, max_sweeps, host_scal, ctas);
+  return w.last_sweeps;
+}
+
+int jacobi_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, double* P,
+                   double* sig, JacobiWork& w, int max_sweeps, double* host_scal, int ctas) {
   const int lp = std::max(2, l + (l & 1));   // even, >= 2; a zero pad row/column never rotates
   const int half = lp / 2;
   int dev = 0, nsm = 0, per_sm = 0;

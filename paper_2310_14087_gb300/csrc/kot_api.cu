@@ -67,7 +67,8 @@ struct kot_ctx {
   JacobiWork jw;
   TcWork tc;
   bool force64 = false;   // mixed form: run the Newton-direction products in FP64 for now
-  long long eig_calls = 0, eig_sweeps = 0;
+  long long eig_calls = 0, eig_sweeps = 0, eig_refined = 0, eig_refine_steps = 0;
+  DevBuf<double> eZ, eP, esig;   // kot_eig_sym: symmetrised input and outputs
   std::vector<double> hist;
   std::vector<double> trace;   // per iteration: ||R||, mu, CG steps, theta, direction kind
   int last_dir_kind = 0;       // 0 FP64, 1 tensor cores, 2 tensor cores + FP64 refinement
@@ -104,6 +105,7 @@ void set_defaults(kot_options* o) {
   o->eig_ctas = 0;
   o->mixed_switch = 1e-4;
   o->batch_workers = 0;
+  o->eig_refine = 5;
 }
 
 bool pos_finite(double v) { return std::isfinite(v) && v > 0.0; }
@@ -205,8 +207,10 @@ void eig_into(kot_ctx* C, const double* Z, EigSlot& e, const EigSlot* warm) {
   const int l = C->l;
   const double* wp = (warm && warm->valid) ? warm->P.p : nullptr;
   C->eig_sweeps += eig_sym_f64(C->st, l, Z, wp, e.P.p, e.sig.p, C->jw, kMaxSweeps, C->hs,
-                               C->opt.eig_ctas);
+                               C->opt.eig_ctas, C->opt.eig_refine);
   C->eig_calls += 1;
+  C->eig_refined += C->jw.last_refine > 0;
+  C->eig_refine_steps += C->jw.last_refine;
   count_nonpos(C->st, l, e.sig.p, C->iscal.p);
   KOT_CUDA(cudaMemcpyAsync(C->hi, C->iscal.p, sizeof(int), cudaMemcpyDeviceToHost, C->st));
   KOT_CUDA(cudaStreamSynchronize(C->st));
@@ -541,7 +545,7 @@ kot_status kot_create(kot_ctx** out, const kot_options* opt) {
   if (o.max_iter < 0 || o.cg_max_iter < 0 || !(o.tau > 0 && o.tau < 1) || !(o.kappa > 0) ||
       !(o.alpha1 > 0) || !(o.alpha2 >= o.alpha1) || !(o.beta0 > 0) || !(o.beta1 > 0) ||
       !(o.beta2 > 0) || !(o.theta0 > 0) || !(o.theta_min > 0) || !(o.theta_max >= o.theta_min) ||
-      !(o.jitter >= 0) || !(o.jitter_max >= o.jitter) || o.eig_ctas < 0 || !(o.mixed_switch >= 0) || o.batch_workers < 0 ||
+      !(o.jitter >= 0) || !(o.jitter_max >= o.jitter) || o.eig_ctas < 0 || !(o.mixed_switch >= 0) || o.batch_workers < 0 || o.eig_refine < 0 ||
       (o.precision != KOT_FP64 && o.precision != KOT_MIXED))
     return KOT_ERR_INVALID;
   int ndev = 0;
@@ -579,11 +583,9 @@ kot_status kot_destroy(kot_ctx* C) {
                             &C->M3, &C->M4, &C->M5, &C->M6, &C->TU, &C->TV, &C->TW, &C->TG,
                             &C->v1, &C->v2, &C->v3, &C->v4, &C->v5, &C->v6, &C->partial,
                             &C->scal, &C->bounds, &C->rw.r1, &C->rw.r2, &C->rv.r1, &C->rv.r2,
-                            &C->rt.r1, &C->rt.r2, &C->jw.A, &C->jw.V, &C->jw.rot, &C->jw.partial,
-                            &C->jw.scal})
+                            &C->rt.r1, &C->rt.r2, &C->eZ, &C->eP, &C->esig})
     b->release();
-  C->jw.bar.release();
-  C->jw.flags.release();
+  C->jw.release();
   C->tc.a.release();
   C->tc.b.release();
   C->tc.err.release();
@@ -593,8 +595,6 @@ kot_status kot_destroy(kot_ctx* C) {
     e->sig.release();
   }
   C->iscal.release();
-  C->jw.pairs.release();
-  C->jw.rank.release();
   if (C->hs) cudaFreeHost(C->hs);
   if (C->hi) cudaFreeHost(C->hi);
   C->prof.release();
@@ -762,6 +762,35 @@ kot_status kot_newton_direction(kot_ctx* C, const double* gamma, const double* X
   });
 }
 
+kot_status kot_eig_sym(kot_ctx* C, int l, const double* Z, const double* warm, double* P,
+                       double* sig, int* info) {
+  if (!C) return KOT_ERR_INVALID;
+  if (l < 1 || !Z || !P || !sig) {
+    C->err = "kot_eig_sym: invalid argument";
+    return KOT_ERR_INVALID;
+  }
+  return run(C, [&] {
+    KOT_CUDA(cudaSetDevice(C->opt.device));
+    const size_t L2 = (size_t)l * l;
+    const double* dZ = dev_in(C, 0, Z, L2);
+    const double* dW = warm ? dev_in(C, 1, warm, L2) : nullptr;
+    C->eZ.alloc(L2);
+    C->eP.alloc(L2);
+    C->esig.alloc((size_t)l);
+    copy_mat(C->st, l, l, dZ, l, C->eZ.p, l);
+    symmetrize(C->st, l, C->eZ.p);
+    eig_sym_f64(C->st, l, C->eZ.p, dW, C->eP.p, C->esig.p, C->jw, kMaxSweeps, C->hs,
+                C->opt.eig_ctas, C->opt.eig_refine);
+    dev_out(C, P, C->eP.p, L2);
+    dev_out(C, sig, C->esig.p, l);
+    KOT_CUDA(cudaStreamSynchronize(C->st));
+    if (info) {
+      info[0] = C->jw.last_sweeps;
+      info[1] = C->jw.last_refine;
+    }
+  });
+}
+
 kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_out,
                          const double* gamma0, const double* X0, kot_result* res) {
   if (!C) return KOT_ERR_INVALID;
@@ -783,7 +812,7 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
     cudaStream_t st = C->st;
     const kot_options& o = C->opt;
     reset_slots(C);
-    C->eig_calls = C->eig_sweeps = 0;
+    C->eig_calls = C->eig_sweeps = C->eig_refined = C->eig_refine_steps = 0;
     if (gamma0) {
       const double* p = dev_in(C, 0, gamma0, l);
       KOT_CUDA(cudaMemcpyAsync(C->g.p, p, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -866,6 +895,8 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
     R.eps = C->eps;
     R.eig_calls = (int)C->eig_calls;
     R.eig_sweeps = (int)C->eig_sweeps;
+    R.eig_refined = (int)C->eig_refined;
+    R.eig_refine_steps = (int)C->eig_refine_steps;
   });
   if (s == KOT_OK && !converged) {
     s = KOT_ERR_NO_CONVERGENCE;

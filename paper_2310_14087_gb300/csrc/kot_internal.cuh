@@ -46,7 +46,8 @@ enum KClass : int {
   KC_GRAM = 5,          // k_gram
   KC_CHOL = 6,          // Cholesky diagonal / panel kernels
   KC_GEMM_TC = 7,       // k_tc_gemm_bf16 (tcgen05 tensor-core GEMM)
-  KC_COUNT = 8
+  KC_REFINE = 8,        // k_refine_correction (eigenbasis refinement step; its GEMMs are gemm_f64)
+  KC_COUNT = 9
 };
 
 // When a profiler is installed for the calling thread, instrumented launch sites record a CUDA
@@ -174,15 +175,32 @@ struct JacobiWork {
   DevBuf<double> partial, scal;
   DevBuf<unsigned> bar;     // grid barrier [arrivals, generation]
   DevBuf<int> flags;        // [error, 2 * sweeps + final buffer]
+  // refinement of a warm basis (l x l each, ld l): ping-pong bases, Z X, X^T Z X, X^T X, I + E
+  DevBuf<double> Xa, Xb, Y, S, G, F, lam;
+  DevBuf<unsigned long long> mx;   // [max |E_ij| (i != j), max |I - X^T X|] as ordered bits
+  int last_sweeps = 0;             // Jacobi sweeps of the last call
+  int last_refine = 0;             // refinement steps of the last call (0: Jacobi was used)
+  void release() {
+    for (DevBuf<double>* b : {&A, &V, &rot, &partial, &scal, &Xa, &Xb, &Y, &S, &G, &F, &lam}) b->release();
+    pairs.release();
+    rank.release();
+    bar.release();
+    flags.release();
+    mx.release();
+  }
 };
 
 // Symmetric eigen-decomposition Z = P diag(sig) P^T, sig ascending.  Z: l x l (full
 // symmetric, read only).  If warm != nullptr its columns (an orthogonal l x l basis, row-major)
 // are used as the starting basis.  P: l x l output (row-major, column j = eigenvector j).
+// With a warm basis the decomposition is first refined from it (at most max_refine steps of
+// the Ogita-Aishima iteration, GEMMs only); if that does not converge quickly it is rebuilt by
+// Jacobi sweeps from the same basis.  w.last_sweeps / w.last_refine report which ran.
 // Returns the number of sweeps taken; throws on non-convergence within max_sweeps.
 // ctas: CTAs of the cooperative launch (0 = one per SM).
 int eig_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, double* P,
-                double* sig, JacobiWork& w, int max_sweeps, double* host_scal, int ctas);
+                double* sig, JacobiWork& w, int max_sweeps, double* host_scal, int ctas,
+                int max_refine);
 
 // ------------------------------------------------------------------ tensor cores (tc_gemm.cu)
 // Logical operand of C = alpha op(A) op(B)^T + beta C: element (r, k) is

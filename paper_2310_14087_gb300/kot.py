@@ -34,7 +34,7 @@ class Options(C.Structure):
                 ("theta_max", C.c_double), ("eg_step", C.c_double), ("jitter", C.c_double),
                 ("jitter_max", C.c_double), ("use_eg", C.c_int), ("record_history", C.c_int),
                 ("eig_ctas", C.c_int), ("mixed_switch", C.c_double),
-                ("batch_workers", C.c_int)]
+                ("batch_workers", C.c_int), ("eig_refine", C.c_int)]
 
 
 class Result(C.Structure):
@@ -42,7 +42,8 @@ class Result(C.Structure):
                 ("eg_taken", C.c_int), ("cg_total", C.c_int), ("residual", C.c_double),
                 ("r1_norm", C.c_double), ("r2_norm", C.c_double), ("objective", C.c_double),
                 ("ot_hat", C.c_double), ("eps", C.c_double), ("seconds", C.c_double),
-                ("eig_calls", C.c_int), ("eig_sweeps", C.c_int)]
+                ("eig_calls", C.c_int), ("eig_sweeps", C.c_int), ("eig_refined", C.c_int),
+                ("eig_refine_steps", C.c_int)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -59,10 +60,10 @@ EXPORTS = ["kot_default_options", "kot_create", "kot_destroy", "kot_last_error",
            "kot_build_features", "kot_set_features", "kot_get_features", "kot_residual",
            "kot_newton_direction", "kot_ssn_solve", "kot_get_history", "kot_batch_solve",
            "kot_profile", "kot_profile_read", "kot_launch_count",
-           "kot_embedding_sqnorm_noalloc", "kot_dense_product", "kot_get_trace"]
+           "kot_embedding_sqnorm_noalloc", "kot_dense_product", "kot_get_trace", "kot_eig_sym"]
 
 KERNEL_CLASSES = ["gemm_f64", "jacobi_f64", "jacobi_f32", "embed", "pair_sums", "gram",
-                  "cholesky", "gemm_tc"]
+                  "cholesky", "gemm_tc", "eig_refine"]
 
 
 class KernelStats(C.Structure):
@@ -99,6 +100,7 @@ def lib() -> C.CDLL:
         "kot_launch_count": (i, [C.POINTER(C.c_longlong)]),
         "kot_dense_product": (i, [vp, i, i, i, d, vp, i, i, vp, i, i, d, vp, i, i]),
         "kot_get_trace": (i, [vp, vp, i, C.POINTER(i)]),
+        "kot_eig_sym": (i, [vp, i, vp, vp, vp, vp, C.POINTER(i)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -222,6 +224,13 @@ class Context:
         return self._check(lib().kot_dense_product(self.h, M, N, K, alpha, _ptr(A), lda, transA,
                                                    _ptr(B), ldb, transB, beta, _ptr(Cm), ldc,
                                                    pieces))
+
+    def eig_sym(self, l, Z, warm, P, sig):
+        """Z = P diag(sig) P^T (sig ascending), refined from `warm` if given.  Returns
+        (Jacobi sweeps, refinement steps) of the call."""
+        info = (C.c_int * 2)()
+        self._check(lib().kot_eig_sym(self.h, l, _ptr(Z), _ptr(warm), _ptr(P), _ptr(sig), info))
+        return info[0], info[1]
 
     def profile(self, mask: int):
         return self._check(lib().kot_profile(self.h, mask))
