@@ -200,6 +200,7 @@ kot_status kot_eig_sym(kot_ctx* ctx, int l, const double* Z, const double* warm,
  * the arithmetic runs on tcgen05 tensor cores in BF16 x BF16 -> FP32 with each operand split
  * into `pieces` BF16 terms (1: BF16 accuracy, about 4e-3 relative; 3: about FP32 accuracy).
  * This is how the mixed form computes the Jacobian-matvec products of Algorithm 1 (Sec. 4.3).
+ * pieces = 0 runs the same product in FP64 on the CUDA cores (the FP64 form's GEMM).
  * Pointers follow the context's pointer mode.  KOT_ERR_TIMEOUT if a tensor-core wait gave up. */
 kot_status kot_dense_product(kot_ctx* ctx, int M, int N, int K, double alpha, const double* A,
                              int lda, int transA, const double* B, int ldb, int transB,

@@ -6,6 +6,9 @@
 // to skip work the triangular Cholesky factor makes zero, not to stage operands for tensor cores.
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "kot_internal.cuh"
 
@@ -70,90 +73,233 @@ void Profiler::release() {
 
 namespace {
 
-constexpr int BK = 32, GT = 64;   // k-chunk and threads per CTA (8 x 8 thread grid)
+// ------------------------------------------------------------------ FP64 GEMM (stream-K)
+// C = alpha op(A) diag(s) op(B) + beta C on the FP64 pipes.  FP64 issue is the bound (two FMA
+// per clock per SM on this part), so the design goal is that every SM sub-partition gets the
+// same number of FMAs: the grid is one CTA of eight warps per SM,
+// the output is cut into 16 x 16 warp tiles, the (tile, k) iterations of all tiles are laid
+// end to end and every warp takes an equal contiguous share ("stream-K").  Two warps share each
+// sub-partition so that one issues while the other waits on memory.  A tile finished by
+// one warp is stored directly; a tile shared by several warps is summed from their partials in
+// warp order by whichever of them arrives last (per-tile arrival counter), so the result does
+// not depend on timing.  Operands are staged per warp through shared memory in k-chunks of 16,
+// the next chunk held in registers while the current one is multiplied.
+constexpr int SK_T = 16, SK_KC = 16, SK_WARPS = 8;
+constexpr int SK_P = SK_T + 2;   // row pitch of the staged tiles (16-byte aligned rows)
 
-// Tile BT x BT (32 or 16); each thread owns a (BT/8) x (BT/8) strided sub-block.  The 16 x 16
-// variant is used when 32 x 32 tiles would leave most of the 152 SMs idle (l of a few hundred).
-template <int BT, bool TA, bool TB>
-__global__ void __launch_bounds__(GT) k_gemm_f64(int M, int N, int K, double alpha,
-                                                 const double* __restrict__ A, int lda,
-                                                 const double* __restrict__ B, int ldb,
-                                                 const double* __restrict__ s, double beta,
-                                                 double* __restrict__ C, int ldc, int flags) {
-  constexpr int TT = BT / 8;
-  const int m0 = blockIdx.y * BT, n0 = blockIdx.x * BT;
-  if ((flags & G_SYM) && n0 < m0) return;
-  __shared__ double As[BK][BT + 1];
-  __shared__ double Bs[BK][BT + 1];
-  int kbeg = 0, kend = K;
-  if (flags & G_KLO_ROW) kbeg = max(kbeg, m0);
-  if (flags & G_KLO_COL) kbeg = max(kbeg, n0);
-  if (flags & G_KHI_COL) kend = min(kend, n0 + BT);
-  if (flags & G_KHI_ROW) kend = min(kend, m0 + BT);
-  const int t = threadIdx.x, tx = t & 7, ty = t >> 3;
-  double acc[TT][TT];
-#pragma unroll
-  for (int i = 0; i < TT; ++i)
-#pragma unroll
-    for (int j = 0; j < TT; ++j) acc[i][j] = 0.0;
+struct SkArgs {
+  int M, N, K, flags;
+  double alpha, beta;
+  const double* A;
+  const double* B;
+  const double* s;
+  double* C;
+  int lda, ldb, ldc;
+  int tn;              // tile columns
+  int ntiles;          // tiles in the work list (upper triangle only for G_SYM)
+  int W;               // warps taking part
+  long long T;         // iterations over all tiles
+  double* part;        // W x 2 x 256 partial tiles
+  unsigned* cnt;       // ntiles arrival counters (zero between launches)
+};
 
-  for (int k0 = (kbeg / BK) * BK; k0 < kend; k0 += BK) {
-#pragma unroll 4
-    for (int r = 0; r < (BT * BK) / GT; ++r) {
-      int idx = t + r * GT;
-      int m, k;
-      if (TA) { k = idx / BT; m = idx % BT; } else { m = idx / BK; k = idx % BK; }
-      int gm = m0 + m, gk = k0 + k;
-      double v = 0.0;
-      if (gm < M && gk >= kbeg && gk < kend) {
-        v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
-        if (s) v *= s[gk];
-      }
-      As[k][m] = v;
-    }
-#pragma unroll 4
-    for (int r = 0; r < (BT * BK) / GT; ++r) {
-      int idx = t + r * GT;
-      int n, k;
-      if (TB) { n = idx / BK; k = idx % BK; } else { k = idx / BT; n = idx % BT; }
-      int gn = n0 + n, gk = k0 + k;
-      double v = 0.0;
-      if (gn < N && gk >= kbeg && gk < kend)
-        v = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
-      Bs[k][n] = v;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int k = 0; k < BK; ++k) {
-      double a[TT], b[TT];
-#pragma unroll
-      for (int i = 0; i < TT; ++i) a[i] = As[k][ty + 8 * i];
-#pragma unroll
-      for (int j = 0; j < TT; ++j) b[j] = Bs[k][tx + 8 * j];
-#pragma unroll
-      for (int i = 0; i < TT; ++i)
-#pragma unroll
-        for (int j = 0; j < TT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
+// Tile t of the work list: origin (m0, n0), k-range [kb, ke) and its length in the iteration
+// space (at least 1, so that a tile with an empty k-range still gets written).
+__host__ __device__ inline void sk_tile(int flags, int K, int tn, int t, int& m0, int& n0, int& kb,
+                                        int& ke, int& len) {
+  int ti, tj;
+  if (flags & G_SYM) {
+    // upper triangle row by row: row i starts at i*tn - i*(i-1)/2
+    const float b = 2.0f * tn + 1.0f;
+    ti = (int)((b - sqrtf(fmaxf(b * b - 8.0f * t, 0.0f))) * 0.5f);   // estimate, fixed below
+    if (ti < 0) ti = 0;
+    while (ti > 0 && (long long)ti * tn - (long long)ti * (ti - 1) / 2 > t) --ti;
+    while ((long long)(ti + 1) * tn - (long long)(ti + 1) * ti / 2 <= t) ++ti;
+    tj = ti + (int)(t - ((long long)ti * tn - (long long)ti * (ti - 1) / 2));
+  } else {
+    ti = t / tn;
+    tj = t - ti * tn;
   }
-  const bool mirror = (flags & G_SYM) && n0 > m0;
+  m0 = ti * SK_T;
+  n0 = tj * SK_T;
+  kb = 0;
+  ke = K;
+  if (flags & G_KLO_ROW) kb = kb > m0 ? kb : m0;
+  if (flags & G_KLO_COL) kb = kb > n0 ? kb : n0;
+  if (flags & G_KHI_COL) ke = ke < n0 + SK_T ? ke : n0 + SK_T;
+  if (flags & G_KHI_ROW) ke = ke < m0 + SK_T ? ke : m0 + SK_T;
+  len = ke - kb > 1 ? ke - kb : 1;
+}
+
+// warp holding iteration g (shares floor(w T / W))
+__device__ __forceinline__ int sk_owner(long long g, long long T, int W) {
+  return (int)(((g + 1) * (long long)W - 1) / T);
+}
+
+// Chunk of 16 k: each operand tile is 16 x 16, eight values per lane, read as rows of 16
+// consecutive doubles (two rows per warp instruction).
+template <bool TA, bool TB>
+__device__ __forceinline__ void sk_load(const SkArgs& a, int m0, int n0, int kc, int kz, int lane,
+                                        double (&ra)[8], double (&rb)[8]) {
 #pragma unroll
-  for (int i = 0; i < TT; ++i) {
-    int gm = m0 + ty + 8 * i;
-    if (gm >= M) continue;
+  for (int q = 0; q < 8; ++q) {
+    int m, k;
+    if (TA) { k = kc + 2 * q + (lane >> 4); m = m0 + (lane & 15); }
+    else { k = kc + (lane & 15); m = m0 + 2 * q + (lane >> 4); }
+    double v = 0.0;
+    if (m < a.M && k < kz) {
+      v = TA ? a.A[(size_t)k * a.lda + m] : a.A[(size_t)m * a.lda + k];
+      if (a.s) v *= a.s[k];
+    }
+    ra[q] = v;
+    int n, kk;
+    if (TB) { kk = kc + (lane & 15); n = n0 + 2 * q + (lane >> 4); }
+    else { kk = kc + 2 * q + (lane >> 4); n = n0 + (lane & 15); }
+    double w = 0.0;
+    if (n < a.N && kk < kz) w = TB ? a.B[(size_t)n * a.ldb + kk] : a.B[(size_t)kk * a.ldb + n];
+    rb[q] = w;
+  }
+}
+
+template <bool TA, bool TB>
+__device__ __forceinline__ void sk_stage(int lane, const double (&ra)[8], const double (&rb)[8],
+                                         double (*sA)[SK_P], double (*sB)[SK_P]) {
 #pragma unroll
-    for (int j = 0; j < TT; ++j) {
-      int gn = n0 + tx + 8 * j;
-      if (gn >= N) continue;
-      double v = alpha * acc[i][j];
-      double* c = &C[(size_t)gm * ldc + gn];
-      *c = (beta == 0.0) ? v : v + beta * (*c);
+  for (int q = 0; q < 8; ++q) {
+    if (TA) sA[2 * q + (lane >> 4)][lane & 15] = ra[q];
+    else sA[lane & 15][2 * q + (lane >> 4)] = ra[q];
+    if (TB) sB[lane & 15][2 * q + (lane >> 4)] = rb[q];
+    else sB[2 * q + (lane >> 4)][lane & 15] = rb[q];
+  }
+}
+
+__device__ __forceinline__ void sk_store(const SkArgs& a, int m0, int n0, int r, int c,
+                                         const double (&acc)[2][4]) {
+  const bool mirror = (a.flags & G_SYM) && n0 > m0;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int gm = m0 + 2 * r + i;
+    if (gm >= a.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + 4 * c + j;
+      if (gn >= a.N) continue;
+      const double v = a.alpha * acc[i][j];
+      double* cp = &a.C[(size_t)gm * a.ldc + gn];
+      *cp = (a.beta == 0.0) ? v : v + a.beta * (*cp);
       if (mirror) {
-        double* cm = &C[(size_t)gn * ldc + gm];
-        *cm = (beta == 0.0) ? v : v + beta * (*cm);
+        double* cm = &a.C[(size_t)gn * a.ldc + gm];
+        *cm = (a.beta == 0.0) ? v : v + a.beta * (*cm);
       }
     }
+  }
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(32 * SK_WARPS, 1) k_gemm_f64_sk(SkArgs a) {
+  __shared__ __align__(16) double sA[SK_WARPS][SK_KC][SK_P];
+  __shared__ __align__(16) double sB[SK_WARPS][SK_KC][SK_P];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int w = wl * gridDim.x + blockIdx.x;   // consecutive shares on different SMs
+  if (w >= a.W) return;
+  const long long g0 = (long long)w * a.T / a.W, g1 = (long long)(w + 1) * a.T / a.W;
+  if (g0 >= g1) return;
+  // locate the tile holding g0: scan the tile lengths 32 at a time
+  int t = 0;
+  long long st = 0;
+  for (int tb = 0; tb < a.ntiles; tb += 32) {
+    int len = 0;
+    if (tb + lane < a.ntiles) {
+      int m0, n0, kb, ke;
+      sk_tile(a.flags, a.K, a.tn, tb + lane, m0, n0, kb, ke, len);
+    }
+    long long incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const long long tot = __shfl_sync(0xffffffffu, incl, 31);
+    if (g0 < st + tot) {
+      const unsigned mask = __ballot_sync(0xffffffffu, st + incl > g0);
+      const int L = __ffs(mask) - 1;
+      const long long incl_L = __shfl_sync(0xffffffffu, incl, L);
+      const int len_L = __shfl_sync(0xffffffffu, len, L);
+      t = tb + L;
+      st += incl_L - len_L;
+      break;
+    }
+    st += tot;
+  }
+  const int r = lane >> 2, c = lane & 3;
+  double (*wA)[SK_P] = sA[wl];
+  double (*wB)[SK_P] = sB[wl];
+  long long g = g0;
+  while (g < g1) {
+    int m0, n0, kb, ke, len;
+    sk_tile(a.flags, a.K, a.tn, t, m0, n0, kb, ke, len);
+    const long long et = st + len, pe = et < g1 ? et : g1;
+    const int ka = kb + (int)(g - st);
+    const int kz = min(ke, kb + (int)(pe - st));
+    double acc[2][4] = {{0.0, 0.0, 0.0, 0.0}, {0.0, 0.0, 0.0, 0.0}};
+    if (ka < kz) {
+      double ra[8], rb[8];
+      sk_load<TA, TB>(a, m0, n0, ka, kz, lane, ra, rb);
+      for (int kc = ka; kc < kz; kc += SK_KC) {
+        __syncwarp();
+        sk_stage<TA, TB>(lane, ra, rb, wA, wB);
+        __syncwarp();
+        if (kc + SK_KC < kz) sk_load<TA, TB>(a, m0, n0, kc + SK_KC, kz, lane, ra, rb);
+        const int nk = min(SK_KC, kz - kc);
+#pragma unroll 4
+        for (int k = 0; k < nk; ++k) {
+          const double2 av = *reinterpret_cast<const double2*>(&wA[k][2 * r]);
+          const double2 b01 = *reinterpret_cast<const double2*>(&wB[k][4 * c]);
+          const double2 b23 = *reinterpret_cast<const double2*>(&wB[k][4 * c + 2]);
+          const double b[4] = {b01.x, b01.y, b23.x, b23.y};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc[0][j] = fma(av.x, b[j], acc[0][j]);
+            acc[1][j] = fma(av.y, b[j], acc[1][j]);
+          }
+        }
+      }
+    }
+    if (g == st && pe == et) {
+      sk_store(a, m0, n0, r, c, acc);
+    } else {
+      // partial tile: slot 0 for the warp's first piece, slot 1 for its last
+      const int slot = (g == g0) ? 0 : 1;
+      double* mine = a.part + ((size_t)w * 2 + slot) * 256 + lane * 8;
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mine[i * 4 + j] = acc[i][j];
+      __threadfence();
+      __syncwarp();
+      const int wa = sk_owner(st, a.T, a.W), wb = sk_owner(et - 1, a.T, a.W);
+      unsigned old = 0;
+      if (lane == 0) old = atomicAdd(&a.cnt[t], 1u);
+      old = __shfl_sync(0xffffffffu, old, 0);
+      if (old == (unsigned)(wb - wa)) {
+        __threadfence();
+        double sum[2][4] = {{0.0, 0.0, 0.0, 0.0}, {0.0, 0.0, 0.0, 0.0}};
+        for (int v = wa; v <= wb; ++v) {
+          const long long gv = (long long)v * a.T / a.W;
+          const int sv = (v == wa && gv < st) ? 1 : 0;
+          const double* src = a.part + ((size_t)v * 2 + sv) * 256 + lane * 8;
+#pragma unroll
+          for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) sum[i][j] += __ldcg(src + i * 4 + j);
+        }
+        sk_store(a, m0, n0, r, c, sum);
+        if (lane == 0) a.cnt[t] = 0u;   // ready for the next launch on this stream
+      }
+    }
+    g = pe;
+    st = et;
+    ++t;
   }
 }
 
@@ -266,31 +412,107 @@ inline int cdiv(size_t a, int b) { return (int)((a + b - 1) / b); }
 
 }  // namespace
 
+namespace {
+
+// Per-stream scratch of the stream-K GEMM (partials and arrival counters).  Launches on one
+// stream are ordered, so one set per stream suffices; counters are left at zero by every launch.
+struct SkWork {
+  DevBuf<double> part;
+  DevBuf<unsigned> cnt;
+};
+std::mutex g_sk_mu;
+std::map<std::pair<int, cudaStream_t>, SkWork> g_sk;
+
+// Multiply-adds the product needs (what the kernel computes, excluding skipped zero blocks):
+// rows m, columns n >= m under G_SYM, and k in [max(lo_row, lo_col), min(hi_row, hi_col)).
+double gemm_macs(int M, int N, int K, int flags) {
+  const bool sym = flags & G_SYM, klc = flags & G_KLO_COL, khc = flags & G_KHI_COL;
+  double macs = 0.0;
+  for (long m = 0; m < M; ++m) {
+    const long a = (flags & G_KLO_ROW) ? m : 0;
+    const long b = (flags & G_KHI_ROW) ? std::min<long>(m + 1, K) : K;
+    const long n0 = sym ? m : 0, n1 = N;
+    if (n0 >= n1 || b <= a) continue;
+    if (!klc && !khc) {
+      macs += (double)(n1 - n0) * (b - a);
+    } else if (klc && !khc) {   // count(n) = b - max(a, n)
+      const long lo = std::max(n0, a), hi = std::min(n1, b);
+      macs += (double)std::max(0L, std::min(n1, a) - n0) * (b - a);
+      if (hi > lo) macs += (double)(hi - lo) * (2 * b - lo - hi + 1) / 2.0;
+    } else if (!klc && khc) {   // count(n) = min(b, n + 1) - a
+      const long lo = std::max(n0, a), hi = std::min(n1, b);
+      if (hi > lo) macs += (double)(hi - lo) * (lo + hi + 1 - 2 * a) / 2.0;
+      macs += (double)std::max(0L, n1 - std::max(n0, b)) * (b - a);
+    } else {
+      for (long n = n0; n < n1; ++n) macs += (double)std::max(0L, std::min(b, n + 1) - std::max(a, n));
+    }
+  }
+  return macs;
+}
+
+}  // namespace
+
 void gemm_f64(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alpha,
               const double* A, int lda, const double* B, int ldb, const double* s, double beta,
               double* C, int ldc, int flags) {
   if (M <= 0 || N <= 0) return;
-  // 32 x 32 tiles unless that gives fewer CTAs than about two per SM
-  const bool small = (size_t)cdiv(N, 32) * cdiv(M, 32) < 2 * 152;
-  const int BT = small ? 16 : 32;
-  dim3 grid(cdiv(N, BT), cdiv(M, BT));
-  ProfScope ps(st, KC_GEMM_F64, 2.0 * M * N * (double)K, 8.0 * ((double)M * K + (double)K * N + (double)M * N));
+  if ((flags & G_SYM) && M != N) throw Error{KOT_ERR_INVALID, "gemm_f64: G_SYM needs M == N"};
+  ProfScope ps(st, KC_GEMM_F64, 2.0 * gemm_macs(M, N, std::max(K, 0), flags),
+               8.0 * ((double)M * K + (double)K * N + (double)M * N));
   if (K <= 0) {   // C = beta C
     if (beta == 0.0)
       for (int i = 0; i < M; ++i) KOT_CUDA(cudaMemsetAsync(C + (size_t)i * ldc, 0, N * sizeof(double), st));
     return;
   }
-#define KOT_GEMM_LAUNCH(BTV)                                                                      \
-  if (!ta && !tb) k_gemm_f64<BTV, false, false><<<grid, GT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, s, beta, C, ldc, flags); \
-  else if (!ta && tb) k_gemm_f64<BTV, false, true><<<grid, GT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, s, beta, C, ldc, flags); \
-  else if (ta && !tb) k_gemm_f64<BTV, true, false><<<grid, GT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, s, beta, C, ldc, flags); \
-  else k_gemm_f64<BTV, true, true><<<grid, GT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, s, beta, C, ldc, flags);
-  if (small) {
-    KOT_GEMM_LAUNCH(16)
-  } else {
-    KOT_GEMM_LAUNCH(32)
+  int dev = 0, nsm = 0;
+  KOT_CUDA(cudaGetDevice(&dev));
+  KOT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  SkArgs a;
+  a.M = M;
+  a.N = N;
+  a.K = K;
+  a.flags = flags;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.A = A;
+  a.B = B;
+  a.s = s;
+  a.C = C;
+  a.lda = lda;
+  a.ldb = ldb;
+  a.ldc = ldc;
+  const int tm = (M + SK_T - 1) / SK_T;
+  a.tn = (N + SK_T - 1) / SK_T;
+  a.ntiles = (flags & G_SYM) ? a.tn * (a.tn + 1) / 2 : tm * a.tn;
+  long long T = 0;
+  for (int t = 0; t < a.ntiles; ++t) {
+    int m0, n0, kb, ke, len;
+    sk_tile(flags, K, a.tn, t, m0, n0, kb, ke, len);
+    T += len;
   }
-#undef KOT_GEMM_LAUNCH
+  a.T = T;
+  // two warps per SM sub-partition when each gets at least 32 k-steps, else one, else fewer
+  // (W <= T keeps every share non-empty, which the arrival count relies on)
+  if (T >= 32LL * SK_WARPS * nsm) a.W = SK_WARPS * nsm;
+  else if (T >= 16LL * (SK_WARPS / 2) * nsm) a.W = (SK_WARPS / 2) * nsm;
+  else a.W = (int)std::max<long long>(1, T / 16);
+  {
+    std::lock_guard<std::mutex> lk(g_sk_mu);
+    SkWork& w = g_sk[{dev, st}];
+    w.part.alloc((size_t)SK_WARPS * nsm * 2 * 256);
+    if (w.cnt.n < (size_t)a.ntiles) {
+      w.cnt.alloc((size_t)a.ntiles);
+      KOT_CUDA(cudaMemsetAsync(w.cnt.p, 0, w.cnt.n * sizeof(unsigned), st));
+    }
+    a.part = w.part.p;
+    a.cnt = w.cnt.p;
+  }
+  const int grid = std::min(nsm, a.W);   // warp w runs in CTA w mod grid
+  if ((long long)grid * SK_WARPS < a.W) throw Error{KOT_ERR_INVALID, "gemm_f64: share count"};
+  if (!ta && !tb) k_gemm_f64_sk<false, false><<<grid, 32 * SK_WARPS, 0, st>>>(a);
+  else if (!ta && tb) k_gemm_f64_sk<false, true><<<grid, 32 * SK_WARPS, 0, st>>>(a);
+  else if (ta && !tb) k_gemm_f64_sk<true, false><<<grid, 32 * SK_WARPS, 0, st>>>(a);
+  else k_gemm_f64_sk<true, true><<<grid, 32 * SK_WARPS, 0, st>>>(a);
   KOT_CHECK_LAUNCH();
 }
 

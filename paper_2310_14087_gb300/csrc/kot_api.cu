@@ -912,7 +912,7 @@ kot_status kot_dense_product(kot_ctx* C, int M, int N, int K, double alpha, cons
                              int lda, int transA, const double* B, int ldb, int transB,
                              double beta, double* Cm, int ldc, int pieces) {
   if (!C) return KOT_ERR_INVALID;
-  if (M < 1 || N < 1 || K < 1 || !A || !B || !Cm || pieces < 1 || pieces > 3 ||
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !Cm || pieces < 0 || pieces > 3 ||
       lda < (transA ? M : K) || ldb < (transB ? N : K) || ldc < N || !std::isfinite(alpha) ||
       !std::isfinite(beta)) {
     C->err = "kot_dense_product: invalid argument";
@@ -929,10 +929,17 @@ kot_status kot_dense_product(kot_ctx* C, int M, int N, int K, double alpha, cons
       KOT_CUDA(cudaMemcpyAsync(C->stage[2].p, Cm, (size_t)M * ldc * sizeof(double), cudaMemcpyHostToDevice, C->st));
       dC = C->stage[2].p;
     }
-    gemm_tc(C->st, C->tc, M, N, K, TcOperand{dA, lda, transA != 0, nullptr},
-            TcOperand{dB, ldb, transB != 0, nullptr}, pieces, alpha, beta, dC, ldc);
+    if (pieces == 0) {
+      // FP64 pipes: gemm_f64 takes op(B) as K x N, i.e. the transpose of this call's op(B)
+      gemm_f64(C->st, transA != 0, transB == 0, M, N, K, alpha, dA, lda, dB, ldb, nullptr, beta, dC,
+               ldc, 0);
+    } else {
+      gemm_tc(C->st, C->tc, M, N, K, TcOperand{dA, lda, transA != 0, nullptr},
+              TcOperand{dB, ldb, transB != 0, nullptr}, pieces, alpha, beta, dC, ldc);
+    }
     if (C->opt.host_pointers) dev_out(C, Cm, dC, (size_t)M * ldc);
-    if (gemm_tc_error(C->st, C->tc)) fail(KOT_ERR_TIMEOUT, "tensor-core GEMM wait timed out");
+    KOT_CUDA(cudaStreamSynchronize(C->st));
+    if (pieces > 0 && gemm_tc_error(C->st, C->tc)) fail(KOT_ERR_TIMEOUT, "tensor-core GEMM wait timed out");
   });
 }
 
