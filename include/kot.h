@@ -201,6 +201,11 @@ kot_status kot_eig_sym(kot_ctx* ctx, int l, const double* Z, const double* warm,
  * into `pieces` BF16 terms (1: BF16 accuracy, about 4e-3 relative; 3: about FP32 accuracy).
  * This is how the mixed form computes the Jacobian-matvec products of Algorithm 1 (Sec. 4.3).
  * pieces = 0 runs the same product in FP64 on the CUDA cores (the FP64 form's GEMM).
+ * pieces = -s (s = 3..8) runs it FP64-accurate on the tensor cores: every row of op(A) and of
+ * op(B) is cut into s fixed-point BF16 slices relative to its largest magnitude, the slice
+ * products of total level < s are summed exactly in FP32 and combined in float-float (error
+ * about 2^-(8 s - 1) max|op(A) row| max|op(B) row| K per element; s = 6 is what the mixed form
+ * uses for its FP64-accuracy products).
  * Pointers follow the context's pointer mode.  KOT_ERR_TIMEOUT if a tensor-core wait gave up. */
 kot_status kot_dense_product(kot_ctx* ctx, int M, int N, int K, double alpha, const double* A,
                              int lda, int transA, const double* B, int ldb, int transB,
@@ -210,7 +215,8 @@ kot_status kot_dense_product(kot_ctx* ctx, int M, int N, int K, double alpha, co
  * Kernel classes: 0 FP64 GEMM tiles, 1 Jacobi eigensolver (FP64, one launch per
  * decomposition), 2 Jacobi eigensolver (FP32), 3 kernel mean
  * embeddings, 4 embedding-norm pair sums, 5 Gram matrices Q and K, 6 Cholesky diagonal block,
- * 7 tensor-core (tcgen05) GEMM tiles.
+ * 7 tensor-core (tcgen05) GEMM tiles, 8 eigenbasis refinement correction, 9 FP64-emulating
+ * tensor-core GEMM (k_oz_gemm), 10 its slicing and finalize kernels.
  * kot_profile(ctx, mask) turns on timing of the classes whose bit is set in mask (0 = off) and
  * clears the statistics.  While on, every launch of an enabled class is bracketed by CUDA events
  * on the context's stream.  kot_profile_read fills, for class cls, the number of launches, the

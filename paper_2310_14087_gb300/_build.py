@@ -10,7 +10,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libkot.so")
-SOURCES = ["dense.cu", "features.cu", "eig.cu", "newton.cu", "tc_gemm.cu", "kot_api.cu", "noalloc.cu"]
+SOURCES = ["dense.cu", "features.cu", "eig.cu", "newton.cu", "tc_gemm.cu", "oz_gemm.cu", "kot_api.cu", "noalloc.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

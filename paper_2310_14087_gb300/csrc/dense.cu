@@ -303,20 +303,28 @@ __global__ void __launch_bounds__(32 * SK_WARPS, 1) k_gemm_f64_sk(SkArgs a) {
   }
 }
 
-__global__ void k_coldot_upper(int l, const double* __restrict__ R, const double* __restrict__ Y,
-                               double* __restrict__ out) {
-  __shared__ double part[8][33];
+// out[i] = sum_{a <= i} R[a,i] Y[a,i]: 32 columns per block, 32 rows of threads striding a
+// (coalesced across i), partial sums reduced through shared memory.
+__global__ void __launch_bounds__(1024) k_coldot_upper(int l, const double* __restrict__ R,
+                                                       const double* __restrict__ Y, double* __restrict__ out) {
+  __shared__ double part[32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int i = blockIdx.x * 32 + tx;
-  double acc = 0.0;
-  if (i < l)
-    for (int a = ty; a <= i; a += 8) acc = fma(R[(size_t)a * l + i], Y[(size_t)a * l + i], acc);
-  part[ty][tx] = acc;
+  double acc0 = 0.0, acc1 = 0.0;
+  if (i < l) {
+    int a = ty;
+    for (; a + 32 <= i; a += 64) {
+      acc0 = fma(R[(size_t)a * l + i], Y[(size_t)a * l + i], acc0);
+      acc1 = fma(R[(size_t)(a + 32) * l + i], Y[(size_t)(a + 32) * l + i], acc1);
+    }
+    if (a <= i) acc0 = fma(R[(size_t)a * l + i], Y[(size_t)a * l + i], acc0);
+  }
+  part[ty][tx] = acc0 + acc1;
   __syncthreads();
   if (ty == 0 && i < l) {
     double s = 0.0;
-#pragma unroll
-    for (int r = 0; r < 8; ++r) s += part[r][tx];
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) s += part[r][tx];
     out[i] = s;
   }
 }
@@ -517,7 +525,7 @@ void gemm_f64(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alp
 }
 
 void coldot_upper(cudaStream_t st, int l, const double* R, const double* Y, double* out) {
-  k_coldot_upper<<<cdiv(l, 32), dim3(32, 8), 0, st>>>(l, R, Y, out);
+  k_coldot_upper<<<cdiv(l, 32), dim3(32, 32), 0, st>>>(l, R, Y, out);
   KOT_CHECK_LAUNCH();
 }
 

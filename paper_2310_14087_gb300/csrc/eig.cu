@@ -55,17 +55,25 @@ __global__ void k_init_pad(int l, int lp, double* __restrict__ A, double* __rest
   V[(size_t)i * lp + j] = v;
 }
 
-// rank_i = #{ j : d_j < d_i or (d_j == d_i and j < i) }  (stable ascending order)
-__global__ void k_rank(int l, int lp, const double* __restrict__ A, int* __restrict__ rank) {
+// rank_i = #{ j : d_j < d_i or (d_j == d_i and j < i) }  (stable ascending order); d_j is read
+// with stride `stride` from `d` (the diagonal of A: stride lp + 1).  The values are staged through
+// shared memory 256 at a time.
+__global__ void k_rank_stride(int l, const double* __restrict__ d, int stride, int* __restrict__ rank) {
+  __shared__ double sh[256];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= l) return;
-  const double di = A[(size_t)i * lp + i];
+  const double di = i < l ? d[(size_t)i * stride] : 0.0;
   int r = 0;
-  for (int j = 0; j < l; ++j) {
-    const double dj = A[(size_t)j * lp + j];
-    r += (dj < di) || (dj == di && j < i);
+  for (int j0 = 0; j0 < l; j0 += 256) {
+    __syncthreads();
+    if (j0 + (int)threadIdx.x < l) sh[threadIdx.x] = d[(size_t)(j0 + threadIdx.x) * stride];
+    __syncthreads();
+    const int n = min(256, l - j0);
+    for (int q = 0; q < n; ++q) {
+      const double dj = sh[q];
+      r += (dj < di) || (dj == di && j0 + q < i);
+    }
   }
-  rank[i] = r;
+  if (i < l) rank[i] = r;
 }
 
 __global__ void k_gather(int l, int lp, const double* __restrict__ A, const double* __restrict__ V,
@@ -87,28 +95,36 @@ __global__ void k_gather(int l, int lp, const double* __restrict__ A, const doub
 // rotated Z and the loss of orthogonality shrink quadratically.  This kernel writes F = I + E,
 // lam, and the largest |E_ij| (i != j) and |delta_ij - G_ij| as ordered bit patterns (a non-finite
 // E orders above every finite value, so it always reads as "not converged").
-__global__ void k_refine_correction(int l, const double* __restrict__ S, const double* __restrict__ G,
+__global__ void k_refine_correction(int l, int ld, const double* __restrict__ S, const double* __restrict__ G,
                                     double* __restrict__ F, double* __restrict__ lam,
                                     unsigned long long* __restrict__ mx) {
   const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
+  // lam_k = S_kk / G_kk for the block's 32 columns and 8 rows, one division each
+  __shared__ double lcol[32], lrow[8];
+  if (threadIdx.y == 0 && j < l) lcol[threadIdx.x] = S[(size_t)j * ld + j] / G[(size_t)j * ld + j];
+  if (threadIdx.y == 1 && threadIdx.x < 8) {
+    const int ii = blockIdx.y * 8 + threadIdx.x;
+    if (ii < l) lrow[threadIdx.x] = S[(size_t)ii * ld + ii] / G[(size_t)ii * ld + ii];
+  }
+  __syncthreads();
   double e_abs = 0.0, r_abs = 0.0;
   if (i < l && j < l) {
-    const size_t ij = (size_t)i * l + j;
+    const size_t ij = (size_t)i * ld + j;
     const double g = G[ij];
-    const double lj = S[(size_t)j * l + j] / G[(size_t)j * l + j];
+    const double lj = lcol[threadIdx.x];
     double f;
     if (i == j) {
       f = 1.0 + 0.5 * (1.0 - g);
       r_abs = fabs(1.0 - g);
       lam[j] = lj;
     } else {
-      const double li = S[(size_t)i * l + i] / G[(size_t)i * l + i];
+      const double li = lrow[threadIdx.y];
       f = (S[ij] - lj * g) / (lj - li);
       e_abs = fabs(f);
       r_abs = fabs(g);
       if (!(e_abs <= 1e300)) e_abs = INFINITY;   // 0/0 or x/0: never converged
     }
-    F[ij] = f;
+    F[(size_t)i * l + j] = f;
   }
   // block maxima (non-negative doubles order like their bit patterns)
   __shared__ unsigned long long sm[2][8];
@@ -133,26 +149,13 @@ __global__ void k_refine_correction(int l, const double* __restrict__ S, const d
   }
 }
 
-// rank_j = #{ i : lam_i < lam_j or (lam_i == lam_j and i < j) }
-__global__ void k_rank_vec(int l, const double* __restrict__ lam, int* __restrict__ rank) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= l) return;
-  const double dj = lam[j];
-  int r = 0;
-  for (int i = 0; i < l; ++i) {
-    const double di = lam[i];
-    r += (di < dj) || (di == dj && i < j);
-  }
-  rank[j] = r;
-}
-
-__global__ void k_gather_vec(int l, const double* __restrict__ lam, const double* __restrict__ X,
+__global__ void k_gather_vec(int l, const double* __restrict__ lam, const double* __restrict__ X, int ldx,
                              const int* __restrict__ rank, double* __restrict__ P,
                              double* __restrict__ sig) {
   const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
   if (i >= l || j >= l) return;
   const int rj = rank[j];
-  P[(size_t)i * l + rj] = X[(size_t)i * l + j];
+  P[(size_t)i * l + rj] = X[(size_t)i * ldx + j];
   if (i == 0) sig[rj] = lam[j];
 }
 
@@ -470,25 +473,55 @@ constexpr double kRefineDone = 1e-8;
 int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, double* P,
                    double* sig, JacobiWork& w, int max_steps) {
   const size_t L2 = (size_t)l * l;
-  for (DevBuf<double>* b : {&w.Xa, &w.Xb, &w.Y, &w.S, &w.G, &w.F}) b->alloc(L2);
+  // FP64 pipes: five products per step, the two symmetric ones on their upper halves only.
+  // Emulated FP64 (w.oz): the basis X sits in the right half of an l x 2l buffer whose left half
+  // receives Z X, so that X^T [Z X | X] gives S and G in one product (launches, not flops, are
+  // what a step costs at moderate l).
+  const bool merged = w.oz != nullptr;
+  const int ldx = merged ? 2 * l : l;
+  for (DevBuf<double>* b : {&w.Xa, &w.Xb, &w.S}) b->alloc(merged ? 2 * L2 : L2);
+  for (DevBuf<double>* b : {&w.Y, &w.G, &w.F}) b->alloc(L2);
   w.lam.alloc((size_t)l);
   w.rank.alloc((size_t)l);
   w.mx.alloc(2);
   const dim3 g2(cdiv(l, 32), cdiv(l, 8)), b2(32, 8);
   const double* X = warm;
+  int ldX = l;
+  if (merged) {
+    copy_mat(st, l, l, warm, l, w.Xa.p + l, ldx);
+    X = w.Xa.p + l;
+    ldX = ldx;
+  }
   for (int k = 0; k < max_steps; ++k) {
-    double* Xn = (k & 1) ? w.Xb.p : w.Xa.p;
-    gemm_f64(st, false, false, l, l, l, 1.0, Z, l, X, l, nullptr, 0.0, w.Y.p, l, 0);       // Y = Z X
-    gemm_f64(st, true, false, l, l, l, 1.0, X, l, w.Y.p, l, nullptr, 0.0, w.S.p, l, G_SYM); // S = X^T Y
-    gemm_f64(st, true, false, l, l, l, 1.0, X, l, X, l, nullptr, 0.0, w.G.p, l, G_SYM);     // G = X^T X
+    const double* S;
+    const double* G;
+    int lds;
+    double* Xn;
+    if (merged) {
+      double* B = (k & 1) ? w.Xb.p : w.Xa.p;            // [Z X | X], X = B + l
+      Xn = ((k & 1) ? w.Xa.p : w.Xb.p) + l;
+      gemm_acc(st, w.oz, false, false, l, l, l, 1.0, Z, l, X, ldX, nullptr, 0.0, B, ldx, 0);     // Z X
+      gemm_acc(st, w.oz, true, false, l, 2 * l, l, 1.0, X, ldX, B, ldx, nullptr, 0.0, w.S.p, ldx, 0);
+      S = w.S.p;                                          // X^T Z X
+      G = w.S.p + l;                                      // X^T X
+      lds = ldx;
+    } else {
+      Xn = (k & 1) ? w.Xb.p : w.Xa.p;
+      gemm_acc(st, w.oz, false, false, l, l, l, 1.0, Z, l, X, ldX, nullptr, 0.0, w.Y.p, l, 0);       // Y = Z X
+      gemm_acc(st, w.oz, true, false, l, l, l, 1.0, X, ldX, w.Y.p, l, nullptr, 0.0, w.S.p, l, G_SYM); // S = X^T Y
+      gemm_acc(st, w.oz, true, false, l, l, l, 1.0, X, ldX, X, ldX, nullptr, 0.0, w.G.p, l, G_SYM);   // G = X^T X
+      S = w.S.p;
+      G = w.G.p;
+      lds = l;
+    }
     KOT_CUDA(cudaMemsetAsync(w.mx.p, 0, 2 * sizeof(unsigned long long), st));
     {
       ProfScope ps(st, KC_REFINE, 12.0 * (double)L2, 8.0 * 3.0 * (double)L2);
-      k_refine_correction<<<g2, b2, 0, st>>>(l, w.S.p, w.G.p, w.F.p, w.lam.p, w.mx.p);
+      k_refine_correction<<<g2, b2, 0, st>>>(l, lds, S, G, w.F.p, w.lam.p, w.mx.p);
       KOT_CHECK_LAUNCH();
       KOT_LAUNCHED(1);
     }
-    gemm_f64(st, false, false, l, l, l, 1.0, X, l, w.F.p, l, nullptr, 0.0, Xn, l, 0);       // X (I + E)
+    gemm_acc(st, w.oz, false, false, l, l, l, 1.0, X, ldX, w.F.p, l, nullptr, 0.0, Xn, ldx, 0);   // X (I + E)
     unsigned long long hm[2] = {0, 0};
     KOT_CUDA(cudaMemcpyAsync(hm, w.mx.p, sizeof(hm), cudaMemcpyDeviceToHost, st));
     KOT_CUDA(cudaStreamSynchronize(st));
@@ -497,9 +530,10 @@ int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
     std::memcpy(&mr, &hm[1], sizeof(double));
     if (!(me <= kRefineGiveUp) || !(mr <= kRefineGiveUp)) return 0;
     X = Xn;
+    ldX = ldx;
     if (me <= kRefineDone && mr <= kRefineDone) {
-      k_rank_vec<<<cdiv(l, 128), 128, 0, st>>>(l, w.lam.p, w.rank.p);
-      k_gather_vec<<<g2, b2, 0, st>>>(l, w.lam.p, X, w.rank.p, P, sig);
+      k_rank_stride<<<cdiv(l, 256), 256, 0, st>>>(l, w.lam.p, 1, w.rank.p);
+      k_gather_vec<<<g2, b2, 0, st>>>(l, w.lam.p, X, ldX, w.rank.p, P, sig);
       KOT_CHECK_LAUNCH();
       KOT_LAUNCHED(2);
       return k + 1;
@@ -552,8 +586,8 @@ int jacobi_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
   dim3 g2(cdiv(lp, 32), cdiv(lp, 8)), b2(32, 8);
   if (warm) {
     // A = warm^T Z warm: V(:, :l) = Z warm (ld lp), then A0 = warm^T V
-    gemm_f64(st, false, false, l, l, l, 1.0, Z, l, warm, l, nullptr, 0.0, w.V.p, lp, 0);
-    gemm_f64(st, true, false, l, l, l, 1.0, warm, l, w.V.p, lp, nullptr, 0.0, A0, lp, G_SYM);
+    gemm_acc(st, w.oz, false, false, l, l, l, 1.0, Z, l, warm, l, nullptr, 0.0, w.V.p, lp, 0);
+    gemm_acc(st, w.oz, true, false, l, l, l, 1.0, warm, l, w.V.p, lp, nullptr, 0.0, A0, lp, G_SYM);
     k_init_pad<<<g2, b2, 0, st>>>(l, lp, A0, w.V.p, nullptr, warm);
   } else {
     k_init_pad<<<g2, b2, 0, st>>>(l, lp, A0, w.V.p, Z, nullptr);
@@ -593,7 +627,7 @@ int jacobi_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
   if (hflags[0] == 2) throw Error{KOT_ERR_NO_CONVERGENCE, "eig: Jacobi did not converge"};
   const int sweeps = hflags[1] / 2, cur = hflags[1] & 1;
   const double* Af = cur ? A1 : A0;
-  k_rank<<<cdiv(l, 128), 128, 0, st>>>(l, lp, Af, w.rank.p);
+  k_rank_stride<<<cdiv(l, 256), 256, 0, st>>>(l, Af, lp + 1, w.rank.p);
   k_gather<<<dim3(cdiv(l, 32), cdiv(l, 8)), b2, 0, st>>>(l, lp, Af, w.V.p, w.rank.p, P, sig);
   KOT_LAUNCHED(2);
   return sweeps;

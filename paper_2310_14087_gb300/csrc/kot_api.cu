@@ -66,6 +66,7 @@ struct kot_ctx {
   int* hi = nullptr;
   JacobiWork jw;
   TcWork tc;
+  OzWork oz;              // mixed form: FP64-accurate products emulated on the tensor cores
   bool force64 = false;   // mixed form: run the Newton-direction products in FP64 for now
   long long eig_calls = 0, eig_sweeps = 0, eig_refined = 0, eig_refine_steps = 0;
   DevBuf<double> eZ, eP, esig;   // kot_eig_sym: symmetrised input and outputs
@@ -154,39 +155,46 @@ void fetch(kot_ctx* C, int count) {
   KOT_CUDA(cudaStreamSynchronize(C->st));
 }
 
+// FP64-accurate products of the mixed form run emulated on the tensor cores (gemm_oz); the FP64
+// form keeps them on the FP64 pipes.
+OzWork* ozp(kot_ctx* C) { return C->opt.precision == KOT_MIXED ? &C->oz : nullptr; }
+
 // ------------------------------------------------------------------ operators (Sec. 4.1)
 // out = Phi*(gamma) = R diag(gamma) R^T
 void phi_star(kot_ctx* C, const double* gamma, double* out) {
   const int l = C->l;
-  gemm_f64(C->st, false, true, l, l, l, 1.0, C->R.p, l, C->R.p, l, gamma, 0.0, out, l,
+  gemm_acc(C->st, ozp(C), false, true, l, l, l, 1.0, C->R.p, l, C->R.p, l, gamma, 0.0, out, l,
            G_KLO_ROW | G_KLO_COL | G_SYM);
 }
 
 // out = Phi(X)_i = (R^T X R)_ii ; tmp: l x l scratch
 void phi(kot_ctx* C, const double* X, double* out, double* tmp) {
   const int l = C->l;
-  gemm_f64(C->st, false, false, l, l, l, 1.0, X, l, C->R.p, l, nullptr, 0.0, tmp, l, G_KHI_COL);
+  gemm_acc(C->st, ozp(C), false, false, l, l, l, 1.0, X, l, C->R.p, l, nullptr, 0.0, tmp, l, G_KHI_COL);
   coldot_upper(C->st, l, C->R.p, tmp, out);
 }
 
 // ---- the same operators on the tensor cores (mixed form, Newton direction only) ----
 bool mixed(const kot_ctx* C) { return C->opt.precision == KOT_MIXED && !C->force64; }
-constexpr int kPieces = 3;   // BF16 pieces per operand: about FP32 accuracy
+// Slices per operand of the reduced-precision Jacobian products inside CG: three BF16 slices,
+// i.e. the six BF16 x BF16 products (FP32 accumulation) of a three-term split, about FP32
+// accuracy; the FP64-accuracy products of the mixed form use oz.slices (six).
+constexpr int kCgSlices = 3;
 
 void phi_star_nd(kot_ctx* C, const double* gamma, double* out) {
   if (!mixed(C)) return phi_star(C, gamma, out);
   const int l = C->l;
   // out[m][n] = sum_k R[m][k] gamma_k R[n][k]
-  gemm_tc(C->st, C->tc, l, l, l, TcOperand{C->R.p, l, false, gamma}, TcOperand{C->R.p, l, false, nullptr},
-          kPieces, 1.0, 0.0, out, l);
+  gemm_oz(C->st, C->oz, l, l, l, TcOperand{C->R.p, l, false, gamma}, TcOperand{C->R.p, l, false, nullptr},
+          kCgSlices, 1.0, 0.0, out, l, true);
 }
 
 void phi_nd(kot_ctx* C, const double* X, double* out, double* tmp) {
   if (!mixed(C)) return phi(C, X, out, tmp);
   const int l = C->l;
   // tmp = X R: tmp[m][n] = sum_k X[m][k] R[k][n]
-  gemm_tc(C->st, C->tc, l, l, l, TcOperand{X, l, false, nullptr}, TcOperand{C->R.p, l, true, nullptr},
-          kPieces, 1.0, 0.0, tmp, l);
+  gemm_oz(C->st, C->oz, l, l, l, TcOperand{X, l, false, nullptr}, TcOperand{C->R.p, l, true, nullptr},
+          kCgSlices, 1.0, 0.0, tmp, l, false);
   coldot_upper(C->st, l, C->R.p, tmp, out);
 }
 
@@ -225,12 +233,12 @@ void form_proj(kot_ctx* C, const double* Z, const EigSlot& e, double* out) {
     fill(C->st, (size_t)l * l, 0.0, out);
   } else if (na <= nb) {
     const double* Pa = e.P.p + nb;
-    gemm_f64(C->st, false, true, l, l, na, 1.0, Pa, l, Pa, l, e.sig.p + nb, 0.0, out, l, G_SYM);
+    gemm_acc(C->st, ozp(C), false, true, l, l, na, 1.0, Pa, l, Pa, l, e.sig.p + nb, 0.0, out, l, G_SYM);
   } else {
     // Pi_{S+}(Z) = Z - P_abar diag(sig_abar) P_abar^T (fewer columns)
     if (out != Z) copy_mat(C->st, l, l, Z, l, out, l);
     if (nb > 0)
-      gemm_f64(C->st, false, true, l, l, nb, -1.0, e.P.p, l, e.P.p, l, e.sig.p, 1.0, out, l, G_SYM);
+      gemm_acc(C->st, ozp(C), false, true, l, l, nb, -1.0, e.P.p, l, e.P.p, l, e.sig.p, 1.0, out, l, G_SYM);
   }
 }
 
@@ -284,23 +292,23 @@ void t_apply(kot_ctx* C, const EigSlot& e, double mu, const double* S, double* o
   const double* Ps = comp ? e.P.p : e.P.p + nb;   // l x rows, ld l
   if (mixed(C)) {
     cudaStream_t st = C->st;
-    TcWork& w = C->tc;
+    OzWork& w = C->oz;
     // U = Ps^T S ; V = U P ; weights ; W = V P^T ; G = Ps W   (C = op(A) op(B)^T form)
-    gemm_tc(st, w, rows, l, l, TcOperand{Ps, l, true, nullptr}, TcOperand{S, l, true, nullptr}, kPieces, 1.0,
-            0.0, C->TU.p, l);
-    gemm_tc(st, w, rows, l, l, TcOperand{C->TU.p, l, false, nullptr}, TcOperand{e.P.p, l, true, nullptr},
-            kPieces, 1.0, 0.0, C->TV.p, l);
+    gemm_oz(st, w, rows, l, l, TcOperand{Ps, l, true, nullptr}, TcOperand{S, l, true, nullptr}, kCgSlices, 1.0,
+            0.0, C->TU.p, l, false);
+    gemm_oz(st, w, rows, l, l, TcOperand{C->TU.p, l, false, nullptr}, TcOperand{e.P.p, l, true, nullptr},
+            kCgSlices, 1.0, 0.0, C->TV.p, l, false);
     t_weights(st, l, nb, e.sig.p, mu, comp ? 1 : 0, C->TV.p);
-    gemm_tc(st, w, rows, l, l, TcOperand{C->TV.p, l, false, nullptr}, TcOperand{e.P.p, l, false, nullptr},
-            kPieces, 1.0, 0.0, C->TW.p, l);
-    gemm_tc(st, w, l, l, rows, TcOperand{Ps, l, false, nullptr}, TcOperand{C->TW.p, l, true, nullptr},
-            kPieces, 1.0, 0.0, C->TG.p, l);
+    gemm_oz(st, w, rows, l, l, TcOperand{C->TV.p, l, false, nullptr}, TcOperand{e.P.p, l, false, nullptr},
+            kCgSlices, 1.0, 0.0, C->TW.p, l, false);
+    gemm_oz(st, w, l, l, rows, TcOperand{Ps, l, false, nullptr}, TcOperand{C->TW.p, l, true, nullptr},
+            kCgSlices, 1.0, 0.0, C->TG.p, l, false);
   } else {
-    gemm_f64(C->st, true, false, rows, l, l, 1.0, Ps, l, S, l, nullptr, 0.0, C->TU.p, l, 0);
-    gemm_f64(C->st, false, false, rows, l, l, 1.0, C->TU.p, l, e.P.p, l, nullptr, 0.0, C->TV.p, l, 0);
+    gemm_acc(C->st, ozp(C), true, false, rows, l, l, 1.0, Ps, l, S, l, nullptr, 0.0, C->TU.p, l, 0);
+    gemm_acc(C->st, ozp(C), false, false, rows, l, l, 1.0, C->TU.p, l, e.P.p, l, nullptr, 0.0, C->TV.p, l, 0);
     t_weights(C->st, l, nb, e.sig.p, mu, comp ? 1 : 0, C->TV.p);
-    gemm_f64(C->st, false, true, rows, l, l, 1.0, C->TV.p, l, e.P.p, l, nullptr, 0.0, C->TW.p, l, 0);
-    gemm_f64(C->st, false, false, l, l, rows, 1.0, Ps, l, C->TW.p, l, nullptr, 0.0, C->TG.p, l, 0);
+    gemm_acc(C->st, ozp(C), false, true, rows, l, l, 1.0, C->TV.p, l, e.P.p, l, nullptr, 0.0, C->TW.p, l, 0);
+    gemm_acc(C->st, ozp(C), false, false, l, l, rows, 1.0, Ps, l, C->TW.p, l, nullptr, 0.0, C->TG.p, l, 0);
   }
   sym_sum(C->st, l, C->TG.p, S, 1.0 / mu, comp ? 1 : 0, out);
 }
@@ -330,14 +338,17 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
   const bool refine = mixed(C);
   int total = 0, refined_steps = 0;
   bool met = false;
+  // right-hand side: a1 = -r1 - Phi(r2 + T[r2])/(mu+1), at2 = -(r2 + T[r2])/(mu+1), formed
+  // once with FP64-accuracy products (CG iterates, not the system, carry the reduced precision)
+  C->force64 = true;
+  t_apply(C, e, mu, r.r2.p, rT);
+  axpby(st, L2, 1.0, r.r2.p, 1.0, rT, rT);
+  phi_nd(C, rT, C->v1.p, C->M2.p);
+  axpby(st, l, -1.0, r.r1.p, -1.0 / (mu + 1.0), C->v1.p, a1);
+  axpby(st, L2, -1.0 / (mu + 1.0), rT, 0.0, nullptr, at2);
+  C->force64 = !allow_tc;
   for (int phase = 0; phase < (refine ? 2 : 1); ++phase) {
     if (phase == 1) C->force64 = true;   // always verify a tensor-core direction in FP64
-    // right-hand side: a1 = -r1 - Phi(r2 + T[r2])/(mu+1), at2 = -(r2 + T[r2])/(mu+1)
-    t_apply(C, e, mu, r.r2.p, rT);
-    axpby(st, L2, 1.0, r.r2.p, 1.0, rT, rT);
-    phi_nd(C, rT, C->v1.p, C->M2.p);
-    axpby(st, l, -1.0, r.r1.p, -1.0 / (mu + 1.0), C->v1.p, a1);
-    axpby(st, L2, -1.0 / (mu + 1.0), rT, 0.0, nullptr, at2);
     if (phase == 0) {
       fill(st, l, 0.0, dgam);
       fill(st, L2, 0.0, TPx);
@@ -472,7 +483,7 @@ double objective_and_ot(kot_ctx* C, const double* gamma, double* ot) {
 void compute_eg_L(kot_ctx* C) {
   const int l = C->l;
   // Kt = R^T R into M1
-  gemm_f64(C->st, true, false, l, l, l, 1.0, C->R.p, l, C->R.p, l, nullptr, 0.0, C->M1.p, l,
+  gemm_acc(C->st, ozp(C), true, false, l, l, l, 1.0, C->R.p, l, C->R.p, l, nullptr, 0.0, C->M1.p, l,
            G_KHI_ROW | G_KHI_COL | G_SYM);
   rowsum_bounds(C->st, l, C->Q.p, C->M1.p, C->bounds.p);
   KOT_CUDA(cudaMemcpyAsync(C->hs, C->bounds.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, C->st));
@@ -514,9 +525,14 @@ kot_status run(kot_ctx* C, const std::function<void()>& body) {
     explicit Install(kot_ctx* c) { set_current_profiler(c && c->prof.mask ? &c->prof : nullptr); }
     ~Install() { set_current_profiler(nullptr); }
   } install(C);
-  if (C) C->force64 = false;
+  if (C) {
+    C->force64 = false;
+    C->jw.oz = C->opt.precision == KOT_MIXED ? &C->oz : nullptr;
+  }
   try {
     body();
+    if (C && C->opt.precision == KOT_MIXED && gemm_oz_error(C->st, C->oz))
+      fail(KOT_ERR_TIMEOUT, "tensor-core FP64-emulation wait timed out");
     return KOT_OK;
   } catch (const Error& e) {
     if (C) C->err = e.what;
@@ -589,6 +605,7 @@ kot_status kot_destroy(kot_ctx* C) {
   C->tc.a.release();
   C->tc.b.release();
   C->tc.err.release();
+  C->oz.release();
   for (auto& b : C->stage) b.release();
   for (EigSlot* e : {&C->ew, &C->ev, &C->et, &C->e1, &C->e2}) {
     e->P.release();
@@ -912,7 +929,8 @@ kot_status kot_dense_product(kot_ctx* C, int M, int N, int K, double alpha, cons
                              int lda, int transA, const double* B, int ldb, int transB,
                              double beta, double* Cm, int ldc, int pieces) {
   if (!C) return KOT_ERR_INVALID;
-  if (M < 1 || N < 1 || K < 1 || !A || !B || !Cm || pieces < 0 || pieces > 3 ||
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !Cm || pieces < -8 || pieces > 3 || pieces == -1 ||
+      pieces == -2 ||
       lda < (transA ? M : K) || ldb < (transB ? N : K) || ldc < N || !std::isfinite(alpha) ||
       !std::isfinite(beta)) {
     C->err = "kot_dense_product: invalid argument";
@@ -933,6 +951,9 @@ kot_status kot_dense_product(kot_ctx* C, int M, int N, int K, double alpha, cons
       // FP64 pipes: gemm_f64 takes op(B) as K x N, i.e. the transpose of this call's op(B)
       gemm_f64(C->st, transA != 0, transB == 0, M, N, K, alpha, dA, lda, dB, ldb, nullptr, beta, dC,
                ldc, 0);
+    } else if (pieces < 0) {
+      gemm_oz(C->st, C->oz, M, N, K, TcOperand{dA, lda, transA != 0, nullptr},
+              TcOperand{dB, ldb, transB != 0, nullptr}, -pieces, alpha, beta, dC, ldc, false);
     } else {
       gemm_tc(C->st, C->tc, M, N, K, TcOperand{dA, lda, transA != 0, nullptr},
               TcOperand{dB, ldb, transB != 0, nullptr}, pieces, alpha, beta, dC, ldc);
@@ -940,6 +961,7 @@ kot_status kot_dense_product(kot_ctx* C, int M, int N, int K, double alpha, cons
     if (C->opt.host_pointers) dev_out(C, Cm, dC, (size_t)M * ldc);
     KOT_CUDA(cudaStreamSynchronize(C->st));
     if (pieces > 0 && gemm_tc_error(C->st, C->tc)) fail(KOT_ERR_TIMEOUT, "tensor-core GEMM wait timed out");
+    if (pieces < 0 && gemm_oz_error(C->st, C->oz)) fail(KOT_ERR_TIMEOUT, "tensor-core GEMM wait timed out");
   });
 }
 

@@ -47,7 +47,9 @@ enum KClass : int {
   KC_CHOL = 6,          // Cholesky diagonal / panel kernels
   KC_GEMM_TC = 7,       // k_tc_gemm_bf16 (tcgen05 tensor-core GEMM)
   KC_REFINE = 8,        // k_refine_correction (eigenbasis refinement step; its GEMMs are gemm_f64)
-  KC_COUNT = 9
+  KC_GEMM_OZ = 9,       // k_oz_gemm (FP64-accurate products emulated on the tensor cores)
+  KC_OZ_AUX = 10,       // k_oz_rowexp + k_oz_split + k_oz_finalize (slicing and FP64 result)
+  KC_COUNT = 11
 };
 
 // When a profiler is installed for the calling thread, instrumented launch sites record a CUDA
@@ -167,7 +169,9 @@ void cholesky_upper_f64(cudaStream_t st, int l, double* A, double eps, int* info
 void rowsum_bounds(cudaStream_t st, int l, const double* Q, const double* Kt, double* out2);
 
 // ------------------------------------------------------------------ eigen (eig.cu)
+struct OzWork;
 struct JacobiWork {
+  OzWork* oz = nullptr;     // non-null: the eigensolver's products are emulated FP64 (tensor cores)
   DevBuf<double> A, V;      // A: two lp x lp buffers; V: lp x lp
   DevBuf<double> rot;       // two rounds x lp/2 pairs x (c, s)
   DevBuf<int> pairs;        // lp
@@ -221,6 +225,37 @@ void gemm_tc(cudaStream_t st, TcWork& w, int M, int N, int K, const TcOperand& A
              const TcOperand& B, int pieces, double alpha, double beta, double* C, int ldc);
 // Nonzero if a tensor-core GEMM CTA timed out since the last call (clears the flag).
 int gemm_tc_error(cudaStream_t st, TcWork& w);
+
+// ------------------------------------------------------------------ FP64 emulation (oz_gemm.cu)
+// FP64-accurate C (M x N, ldc) = alpha * sum_k opA(r=m, k) opB(r=n, k) + beta * C on the tensor
+// cores: every operand row is cut into `slices` (3..8) fixed-point BF16 slices whose products
+// are summed exactly in FP32 and combined in float-float (error about 2^-(8 slices - 1) relative to
+// max|A row| max|B row| K).  sym: the result is symmetric (M == N); it is made exactly so.
+struct OzWork {
+  DevBuf<unsigned short> a, b;   // sliced operands
+  DevBuf<int> part;              // per-row exponent partials
+  DevBuf<double> fac;            // per-row scale factors
+  DevBuf<float2> w;              // per-split partial sums
+  DevBuf<int> err;               // set by a CTA whose bounded wait gave up
+  int slices = 6;
+  void release() {
+    a.release();
+    b.release();
+    part.release();
+    fac.release();
+    w.release();
+    err.release();
+  }
+};
+void gemm_oz(cudaStream_t st, OzWork& w, int M, int N, int K, const TcOperand& A, const TcOperand& B,
+             int slices, double alpha, double beta, double* C, int ldc, bool sym);
+int gemm_oz_error(cudaStream_t st, OzWork& w);
+// gemm_f64's interface (C = alpha opA(A) diag(s) opB(B) + beta C, triangular/symmetric flags):
+// on the FP64 pipes when oz is null, else emulated on the tensor cores with oz->slices slices
+// (the triangular flags only cut work on the FP64 pipes; G_SYM is honoured by both).
+void gemm_acc(cudaStream_t st, OzWork* oz, bool ta, bool tb, int M, int N, int K, double alpha,
+              const double* A, int lda, const double* B, int ldb, const double* s, double beta,
+              double* C, int ldc, int flags);
 
 // ------------------------------------------------------------------ Newton pieces (newton.cu)
 // Scale rows of V (na x l) for the G + G^T form of T: columns in alpha by 1/(2 mu), columns in

@@ -1,0 +1,634 @@
+// FP64-accurate dense products on the tcgen05 tensor cores:
+//   C = alpha * opA(A) * opB(B)^T + beta * C,   FP64 in, FP64 out,
+// computed from exact BF16 x BF16 products summed exactly in FP32 (the splitting idea of Ozaki,
+// Ogita and Oishi, Numer. Algorithms 59, 2012: cut each operand into fixed-point slices whose
+// pairwise products are error-free on a low-precision multiplier, multiply slice by slice, and
+// add the partial products in higher precision).
+//
+// Why: this GPU issues about two FP64 FMAs per clock per SM (1.2 TFLOP/s in all), so every
+// O(l^3) FP64 product of the mixed form would otherwise run at ~1/1600 of the BF16 tensor rate.
+//
+// Slicing.  Logical row r of an operand (its K values, times the optional scale vector) has
+// binary exponent e_r with max_k |v(r,k)| < 2^e_r.  Each value is rounded to the fixed-point
+// integer X = round(|v| 2^(7 + 8 (s - 1) - e_r)) and X is written in balanced base-256 digits
+// d_0 .. d_(s-1) with |d_i| <= 128, so that
+//     v ~ 2^(e_r - 7) * sum_i d_i 2^(-8 i)          (error <= 2^(e_r - 8 s) per value).
+// Slice i holds the BF16 value d_i 2^(-8 i), which is exact (at most 8 significant bits).
+// The product of slice i of A and slice j of B ("level" t = i + j) is an integer of magnitude
+// <= 2^14 times 2^(-8 t).  Levels t >= s are dropped (they are below the slicing error).
+//
+// Exact accumulation.  Terms of one level summed in FP32 stay exact while the integer sum stays
+// <= 2^24, i.e. for up to 1024 products; the kernel closes an accumulation group after at most
+// OZ_EXACT_TILES x 64 = 512 of them and never mixes levels in a group for t < OZ_EXACT_LEVELS.
+// Levels >= OZ_EXACT_LEVELS (weight <= 2^-32 of level 0) share one FP32 group: its rounding is
+// far below the slicing error.  Each finished group is read out of tensor memory and added to a
+// float-float (hi, lo) pair per output element with an error-free two-sum, so the combination of
+// groups costs FP32 additions only (FP64 would cost a clock per two elements on this part).
+// Net accuracy: about 2^-47 relative to max_k |A(r,k)| * max_k |B(c,k)| * K per element for
+// s = 6, i.e. FP64 GEMM accuracy up to a small factor.
+//
+// Kernels: (1) per-row exponent partials, (2) slicing into a BF16 operand matrix [rows][s * Kp]
+// (slice i occupies columns i * Kp .. i * Kp + Kp - 1), (3) the tcgen05 GEMM: one CTA per
+// 128 x 64 output tile and split z of the slice pairs; warp 4 streams 128 x 64 (A) and 64 x 64
+// (B) BF16 tiles with TMA into a 6-stage ring, warp 5 issues tcgen05.mma (M 128, N 64, K 16)
+// into one of two 64-column FP32 accumulators in tensor memory and hands each finished group
+// to warps 0-3, which drain it while the next group accumulates in the other buffer; the
+// (hi, lo) pairs of each split go to a float2 buffer; (4) finalize: sum the splits, convert to
+// FP64, scale by alpha 2^(e_r - 7) 2^(e_c - 7), add beta C.  Every wait is bounded.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "kot_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace kot {
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 64, OZ_STAGES = 6, OZ_THREADS = 192;
+constexpr int OZ_A_BYTES = OZ_BM * OZ_BK * 2;   // 16 KB
+constexpr int OZ_B_BYTES = OZ_BN * OZ_BK * 2;   // 8 KB
+constexpr int OZ_STAGE = OZ_A_BYTES + OZ_B_BYTES;
+constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + 1024 + 256;
+constexpr int OZ_TMEM_COLS = 2 * OZ_BN;          // two accumulator buffers
+constexpr int OZ_EXACT_LEVELS = 4;
+constexpr int OZ_EXACT_TILES = 8;                // 8 x 64 products of |.| <= 2^14: sum <= 2^23
+constexpr int OZ_MAX_SLICES = 8;
+constexpr int OZ_MAX_PAIRS = OZ_MAX_SLICES * (OZ_MAX_SLICES + 1) / 2;
+constexpr int OZ_MAX_SPLITS = 8;
+constexpr int kOzClusterK = 8 * 64;   // K up to which one (portable, <= 8 block) cluster spans a row
+
+inline int cdiv(size_t a, int b) { return (int)((a + b - 1) / b); }
+
+struct OzPlan {
+  int M, N, Kp, nk, npairs;
+  int pbeg[OZ_MAX_SPLITS + 1];        // split z takes slice pairs [pbeg[z], pbeg[z + 1])
+  signed char pa[OZ_MAX_PAIRS], pb[OZ_MAX_PAIRS], lv[OZ_MAX_PAIRS];
+  float2* W;                          // splits x M x N partial sums (hi, lo)
+  int* err;
+};
+
+// Does the tile of level lv (following a tile of level prev; gt tiles already in the current
+// group) start a new accumulation group?
+__device__ __forceinline__ bool oz_new_group(int prev, int lv, int gt) {
+  if (gt == 0) return true;
+  if (lv != prev && (lv < OZ_EXACT_LEVELS || prev < OZ_EXACT_LEVELS)) return true;
+  return lv < OZ_EXACT_LEVELS && gt >= OZ_EXACT_TILES;
+}
+
+// (hi, lo) += g with Knuth's error-free two-sum on hi; rounding is pinned (no contraction).
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float g) {
+  const float s = __fadd_rn(hi, g);
+  const float bp = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(g, bp));
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    k_oz_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+              const __grid_constant__ OzPlan P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + OZ_STAGES * OZ_STAGE);
+  uint64_t* empty = full + OZ_STAGES;
+  uint64_t* acc_full = empty + OZ_STAGES;   // [2]: group in buffer b is complete
+  uint64_t* acc_empty = acc_full + 2;       // [2]: buffer b has been read out (4 warp arrivals)
+  uint64_t* done = acc_empty + 2;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * OZ_BM, n0 = blockIdx.x * OZ_BN, z = blockIdx.z;
+  const int p0 = P.pbeg[z], p1 = P.pbeg[z + 1];
+  const int nk = P.nk;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, OZ_TMEM_COLS);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  if (warp == 4) {
+    if (lane == 0) {
+      // TMA producer: the tiles of every slice pair of this split, in order
+      int n = 0;
+      for (int p = p0; p < p1 && ok; ++p) {
+        const int xa = P.pa[p] * P.Kp, xb = P.pb[p] * P.Kp;
+        for (int kt = 0; kt < nk; ++kt, ++n) {
+          const int s = n % OZ_STAGES;
+          const uint32_t ph = (uint32_t)(n / OZ_STAGES) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], OZ_STAGE);
+          uint8_t* st = smem + s * OZ_STAGE;
+          tma_load_2d(st, &ta, &full[s], xa + kt * OZ_BK, m0);
+          tma_load_2d(st + OZ_A_BYTES, &tb, &full[s], xb + kt * OZ_BK, n0);
+        }
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      // MMA issuer
+      constexpr uint32_t idesc = idesc_bf16(OZ_BM, OZ_BN);
+      int n = 0, g = -1, gt = 0, prev = -1;
+      for (int p = p0; p < p1 && ok; ++p) {
+        const int lv = P.lv[p];
+        for (int kt = 0; kt < nk; ++kt, ++n) {
+          const bool first = oz_new_group(prev, lv, gt);
+          if (first) {
+            if (g >= 0) umma_commit(&acc_full[g & 1]);
+            ++g;
+            gt = 0;
+            // the buffer must have been read out (group g - 2) before it is overwritten
+            if (!mbar_wait(&acc_empty[g & 1], (((uint32_t)g >> 1) & 1u) ^ 1u)) {
+              ok = false;
+              break;
+            }
+          }
+          const int s = n % OZ_STAGES;
+          const uint32_t ph = (uint32_t)(n / OZ_STAGES) & 1u;
+          if (!mbar_wait(&full[s], ph)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a_addr = smem_u32(smem + s * OZ_STAGE);
+          const uint32_t b_addr = a_addr + OZ_A_BYTES;
+          const uint32_t d = tmem + (uint32_t)((g & 1) * OZ_BN);
+#pragma unroll
+          for (int k = 0; k < OZ_BK / 16; ++k)
+            umma_bf16(d, smem_desc_sw128(a_addr + 32 * k), smem_desc_sw128(b_addr + 32 * k), idesc,
+                      (first && k == 0) ? 0u : 1u);
+          umma_commit(&empty[s]);
+          ++gt;
+          prev = lv;
+        }
+      }
+      if (g >= 0 && ok) umma_commit(&acc_full[g & 1]);
+      // every MMA of this thread has completed before tensor memory is released
+      umma_commit(done);
+      if (!mbar_wait(done, 0)) ok = false;
+    }
+  } else {
+    // epilogue warps 0-3: warp w owns accumulator lanes (output rows) 32 w .. 32 w + 31
+    int G = 0;
+    {
+      int gt = 0, prev = -1;
+      for (int p = p0; p < p1; ++p) {
+        const int lv = P.lv[p];
+        for (int kt = 0; kt < nk; ++kt) {
+          if (oz_new_group(prev, lv, gt)) {
+            ++G;
+            gt = 0;
+          }
+          ++gt;
+          prev = lv;
+        }
+      }
+    }
+    float hi[OZ_BN], lo[OZ_BN];
+#pragma unroll
+    for (int j = 0; j < OZ_BN; ++j) hi[j] = lo[j] = 0.0f;
+    for (int g = 0; g < G; ++g) {
+      if (!mbar_wait(&acc_full[g & 1], ((uint32_t)g >> 1) & 1u)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((g & 1) * OZ_BN);
+#pragma unroll
+      for (int h = 0; h < OZ_BN / 32; ++h) {
+        uint32_t r[32];
+        tmem_ld_32cols(base + 32 * h, r);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) ff_add(hi[32 * h + j], lo[32 * h + j], __uint_as_float(r[j]));
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[g & 1]);
+    }
+    const int row = m0 + warp * 32 + lane;
+    if (ok && row < P.M) {
+      float2* wr = P.W + ((size_t)z * P.M + row) * P.N;
+#pragma unroll
+      for (int j = 0; j < OZ_BN; ++j)
+        if (n0 + j < P.N) wr[n0 + j] = make_float2(hi[j], lo[j]);
+    }
+  }
+  if (!ok) atomicExch(P.err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, OZ_TMEM_COLS);
+}
+
+// ------------------------------------------------------------------ slicing
+// Logical operand: element (r, k) = (trans ? src[k ld + r] : src[r ld + k]) * (scale ? scale[k] : 1)
+// for r < rows, k < K.
+struct OzOperand {
+  int rows, K;
+  const double* src;
+  int ld, trans;
+  const double* scale;
+  int* part;                 // ceil(K / 64) x rows exponent partials
+  __nv_bfloat16* out;        // rows x (s * Kp)
+  double* fac;               // rows: mult * 2^(e_r - 7)
+  double mult;
+};
+struct OzSplitArgs {
+  OzOperand op[2];
+  int Kp, s;
+};
+
+__device__ __forceinline__ int biased_exp(double v) {
+  return (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FFu);
+}
+
+__device__ __forceinline__ double oz_load(const OzOperand& o, int r, int k) {
+  double v = o.trans ? o.src[(size_t)k * o.ld + r] : o.src[(size_t)r * o.ld + k];
+  if (o.scale) v *= o.scale[k];
+  return v;
+}
+
+// part[kb][r] = max biased exponent of v(r, k) over the 64 k of block kb
+__global__ void k_oz_rowexp(OzSplitArgs a) {
+  const OzOperand& o = a.op[blockIdx.z];
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
+  if (r0 >= o.rows || k0 >= o.K) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  if (o.trans) {
+    __shared__ int sm[8][33];
+    const int r = r0 + tx;
+    int e = 0;
+    if (r < o.rows)
+      for (int kk = ty; kk < 64; kk += 8) {
+        const int k = k0 + kk;
+        if (k < o.K) e = max(e, biased_exp(oz_load(o, r, k)));
+      }
+    sm[ty][tx] = e;
+    __syncthreads();
+    if (ty == 0 && r < o.rows) {
+#pragma unroll
+      for (int y = 1; y < 8; ++y) e = max(e, sm[y][tx]);
+      o.part[(size_t)blockIdx.x * o.rows + r] = e;
+    }
+  } else {
+    for (int i = ty; i < 32; i += 8) {
+      const int r = r0 + i;
+      int e = 0;
+      if (r < o.rows)
+        for (int kk = tx; kk < 64; kk += 32) {
+          const int k = k0 + kk;
+          if (k < o.K) e = max(e, biased_exp(oz_load(o, r, k)));
+        }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, off));
+      if (tx == 0 && r < o.rows) o.part[(size_t)blockIdx.x * o.rows + r] = e;
+    }
+  }
+}
+
+// Balanced base-256 digits of v relative to the row exponent er (max |v| < 2^er):
+// |v| 2^(7 + 8 (s-1) - er) rounded to the integer X = sum_i d_i 256^(s-1-i), |d_i| <= 128.
+// Integer arithmetic only (FP64 issue is scarce on this part).
+__device__ __forceinline__ void oz_digits(double v, int er, int s, int (&d)[OZ_MAX_SLICES]) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  int E = (int)((b >> 52) & 0x7FFu);
+  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  if (E == 0) E = 1;             // subnormal: no implicit bit
+  else m |= 1ull << 52;          // |v| = m 2^(E - 1075)
+  const int sh = 1075 - E - 7 - 8 * (s - 1) + er;
+  unsigned long long X;
+  if (sh >= 64) X = 0;
+  else if (sh > 0) X = (m >> sh) + ((m >> (sh - 1)) & 1ull);
+  else X = m << (-sh);
+#pragma unroll
+  for (int i = OZ_MAX_SLICES - 1; i >= 1; --i) {
+    d[i] = 0;
+    if (i < s) {
+      int dd = (int)(X & 0xFFu);
+      X >>= 8;
+      if (dd >= 128) {
+        dd -= 256;
+        ++X;
+      }
+      d[i] = dd;
+    }
+  }
+  d[0] = (int)X;
+  if (b >> 63)
+#pragma unroll
+    for (int i = 0; i < OZ_MAX_SLICES; ++i) d[i] = -d[i];
+}
+
+// Slicing for K > kOzClusterK: row exponents from the partials of k_oz_rowexp.
+__global__ void k_oz_split(OzSplitArgs a) {
+  const OzOperand& o = a.op[blockIdx.z];
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  if (r0 >= o.rows) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  const int s = a.s, Kp = a.Kp;
+  __shared__ double tile[32][33];
+  __shared__ int se[32];
+  if (ty == 0) {
+    const int r = r0 + tx;
+    int E = 0;
+    if (r < o.rows) {
+      const int nkb = (o.K + 63) / 64;
+      for (int kb = 0; kb < nkb; ++kb) E = max(E, o.part[(size_t)kb * o.rows + r]);
+    }
+    if (blockIdx.x == 0 && r < o.rows)
+      o.fac[r] = (E == 0x7FF) ? __longlong_as_double(0x7FF8000000000000ll) : ldexp(o.mult, E - 1022 - 7);
+    se[tx] = E - 1022;   // row exponent e_r
+  }
+  for (int i = ty; i < 32; i += 8) {
+    if (o.trans) {
+      const int k = k0 + i, r = r0 + tx;
+      tile[tx][i] = (k < o.K && r < o.rows) ? o.src[(size_t)k * o.ld + r] : 0.0;
+    } else {
+      const int r = r0 + i, k = k0 + tx;
+      tile[i][tx] = (k < o.K && r < o.rows) ? o.src[(size_t)r * o.ld + k] : 0.0;
+    }
+  }
+  __syncthreads();
+  const size_t rowlen = (size_t)s * Kp;
+  for (int i = ty; i < 32; i += 8) {
+    const int r = r0 + i, k = k0 + tx;
+    if (r >= o.rows || k >= Kp) continue;
+    double v = tile[i][tx];
+    if (o.scale && k < o.K) v *= o.scale[k];
+    int d[OZ_MAX_SLICES];
+    oz_digits(v, se[i], s, d);
+    __nv_bfloat16* dst = o.out + (size_t)r * rowlen + k;
+#pragma unroll
+    for (int j = 0; j < OZ_MAX_SLICES; ++j) {
+      if (j < s) {
+        // d_j 2^(-8 j): at most 8 significant bits, so the BF16 truncation is exact
+        const float f = __int2float_rn(d[j]) * __int_as_float((127 - 8 * j) << 23);
+        dst[(size_t)j * Kp] = __ushort_as_bfloat16((unsigned short)(__float_as_uint(f) >> 16));
+      }
+    }
+  }
+}
+
+// Slicing for K <= kOzClusterK in one launch: a cluster of ceil(K / 64) blocks spans the K range
+// of 32 logical rows.  Each block keeps its 32 x 64 values in shared memory, publishes its
+// per-row maximum exponents, reads its peers' through distributed shared memory, and slices its
+// own values (no second pass over the operand, no second launch).  All blocks of a cluster share
+// blockIdx.y and blockIdx.z, so a cluster is either wholly inside the operand or wholly outside.
+__global__ void k_oz_split_cluster(OzSplitArgs a) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const OzOperand& o = a.op[blockIdx.z];
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
+  if (r0 >= o.rows) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  const int s = a.s, Kp = a.Kp;
+  __shared__ double tile[32][65];                 // [row][k - k0]
+  __shared__ int pmax[32], se[32];
+  if (o.trans) {
+    const int r = r0 + tx;
+#pragma unroll
+    for (int kk = ty; kk < 64; kk += 8) {
+      const int k = k0 + kk;
+      tile[tx][kk] = (k < o.K && r < o.rows) ? oz_load(o, r, k) : 0.0;
+    }
+  } else {
+#pragma unroll
+    for (int i = ty; i < 32; i += 8) {
+      const int r = r0 + i;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = k0 + tx + 32 * h;
+        tile[i][tx + 32 * h] = (k < o.K && r < o.rows) ? oz_load(o, r, k) : 0.0;
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = ty; i < 32; i += 8) {
+    int e = max(biased_exp(tile[i][tx]), biased_exp(tile[i][tx + 32]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, off));
+    if (tx == 0) pmax[i] = e;
+  }
+  cluster.sync();
+  if (ty == 0) {
+    int E = 0;
+    for (unsigned q = 0; q < cluster.num_blocks(); ++q) E = max(E, cluster.map_shared_rank(pmax, q)[tx]);
+    const int r = r0 + tx;
+    if (blockIdx.x == 0 && r < o.rows)
+      o.fac[r] = (E == 0x7FF) ? __longlong_as_double(0x7FF8000000000000ll) : ldexp(o.mult, E - 1022 - 7);
+    se[tx] = E - 1022;
+  }
+  cluster.sync();   // peers are done reading pmax; se is visible block-wide
+  const size_t rowlen = (size_t)s * Kp;
+#pragma unroll
+  for (int i = ty; i < 32; i += 8) {
+    const int r = r0 + i;
+    if (r >= o.rows) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = k0 + tx + 32 * h;
+      if (k >= Kp) continue;
+      int d[OZ_MAX_SLICES];
+      oz_digits(tile[i][tx + 32 * h], se[i], s, d);
+      __nv_bfloat16* dst = o.out + (size_t)r * rowlen + k;
+#pragma unroll
+      for (int j = 0; j < OZ_MAX_SLICES; ++j)
+        if (j < s) {
+          const float f = __int2float_rn(d[j]) * __int_as_float((127 - 8 * j) << 23);
+          dst[(size_t)j * Kp] = __ushort_as_bfloat16((unsigned short)(__float_as_uint(f) >> 16));
+        }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ finalize
+__device__ __forceinline__ double oz_value(const float2* __restrict__ W, size_t MN, int splits, size_t idx) {
+  float2 w = W[idx];
+  float hi = w.x, lo = w.y;
+  for (int z = 1; z < splits; ++z) {
+    const float2 u = W[(size_t)z * MN + idx];
+    ff_add(hi, lo, u.x);
+    lo = __fadd_rn(lo, u.y);
+  }
+  return (double)hi + (double)lo;
+}
+
+__global__ void k_oz_finalize(int M, int N, int splits, const float2* __restrict__ W,
+                              const double* __restrict__ fa, const double* __restrict__ fb, double beta,
+                              double* __restrict__ C, int ldc, int sym) {
+  const size_t MN = (size_t)M * N;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < MN;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / N), c = (int)(idx - (size_t)r * N);
+    if (sym && c < r) continue;
+    double v = oz_value(W, MN, splits, idx) * fa[r] * fb[c];
+    if (sym && c != r) {
+      const double u = oz_value(W, MN, splits, (size_t)c * N + r) * fa[c] * fb[r];
+      v = 0.5 * (v + u);
+      double* cm = C + (size_t)c * ldc + r;
+      *cm = (beta == 0.0) ? v : fma(beta, *cm, v);
+    }
+    double* cp = C + (size_t)r * ldc + c;
+    *cp = (beta == 0.0) ? v : fma(beta, *cp, v);
+  }
+}
+
+}  // namespace
+
+void gemm_oz(cudaStream_t st, OzWork& w, int M, int N, int K, const TcOperand& A, const TcOperand& B,
+             int slices, double alpha, double beta, double* C, int ldc, bool sym) {
+  if (M <= 0 || N <= 0) return;
+  if (slices < 3 || slices > OZ_MAX_SLICES) throw Error{KOT_ERR_INVALID, "gemm_oz: slices must be 3..8"};
+  if (sym && M != N) throw Error{KOT_ERR_INVALID, "gemm_oz: a symmetric result needs M == N"};
+  if (K <= 0) {
+    if (beta == 0.0)
+      for (int i = 0; i < M; ++i) KOT_CUDA(cudaMemsetAsync(C + (size_t)i * ldc, 0, N * sizeof(double), st));
+    return;
+  }
+  const int s = slices;
+  const int Kp = cdiv(K, OZ_BK) * OZ_BK;
+  const int nkb = cdiv(K, 64);
+  int dev = 0, nsm = 0;
+  KOT_CUDA(cudaGetDevice(&dev));
+  KOT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+
+  OzPlan P;
+  P.M = M;
+  P.N = N;
+  P.Kp = Kp;
+  P.nk = Kp / OZ_BK;
+  int np = 0;
+  for (int t = 0; t < s; ++t)
+    for (int i = 0; i <= t; ++i) {
+      P.pa[np] = (signed char)i;
+      P.pb[np] = (signed char)(t - i);
+      P.lv[np] = (signed char)t;
+      ++np;
+    }
+  P.npairs = np;
+  const int tiles = cdiv(N, OZ_BN) * cdiv(M, OZ_BM);
+  const int splits = std::max(1, std::min({OZ_MAX_SPLITS, np, nsm / tiles}));
+  for (int z = 0; z <= splits; ++z) P.pbeg[z] = z * np / splits;
+
+  w.a.alloc((size_t)M * s * Kp);
+  w.b.alloc((size_t)N * s * Kp);
+  w.part.alloc((size_t)nkb * (M + N));
+  w.fac.alloc((size_t)M + N);
+  w.w.alloc((size_t)splits * M * N);
+  if (!w.err.p) {
+    w.err.alloc(1);
+    KOT_CUDA(cudaMemsetAsync(w.err.p, 0, sizeof(int), st));
+  }
+  P.W = w.w.p;
+  P.err = w.err.p;
+
+  OzSplitArgs sa;
+  sa.Kp = Kp;
+  sa.s = s;
+  const TcOperand* ops[2] = {&A, &B};
+  const int rows[2] = {M, N};
+  for (int q = 0; q < 2; ++q) {
+    OzOperand& o = sa.op[q];
+    o.rows = rows[q];
+    o.K = K;
+    o.src = ops[q]->src;
+    o.ld = ops[q]->ld;
+    o.trans = ops[q]->trans ? 1 : 0;
+    o.scale = ops[q]->scale;
+    o.part = w.part.p + (q == 0 ? 0 : (size_t)nkb * M);
+    o.out = (__nv_bfloat16*)(q == 0 ? w.a.p : w.b.p);
+    o.fac = w.fac.p + (q == 0 ? 0 : M);
+    o.mult = q == 0 ? alpha : 1.0;
+  }
+  const int rb = cdiv(std::max(M, N), 32);
+  const dim3 bs(32, 8);
+  {
+    // bytes: FP64 operands read twice, BF16 slices written
+    ProfScope ps(st, KC_OZ_AUX, 0.0, 16.0 * ((double)M + N) * K + 2.0 * s * ((double)M + N) * Kp);
+    if (K <= kOzClusterK) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(nkb, rb, 2);
+      cfg.blockDim = bs;
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = (unsigned)nkb;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      KOT_CUDA(cudaLaunchKernelEx(&cfg, k_oz_split_cluster, sa));
+      KOT_LAUNCHED(1);
+    } else {
+      k_oz_rowexp<<<dim3(nkb, rb, 2), bs, 0, st>>>(sa);
+      k_oz_split<<<dim3(Kp / 32, rb, 2), bs, 0, st>>>(sa);
+      KOT_LAUNCHED(2);
+    }
+  }
+
+  const CUtensorMap ta = make_bf16_map(w.a.p, M, s * Kp, OZ_BM);
+  const CUtensorMap tb = make_bf16_map(w.b.p, N, s * Kp, OZ_BN);
+  static bool attr_set = false;
+  if (!attr_set) {
+    KOT_CUDA(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+    attr_set = true;
+  }
+  {
+    // tensor work: np BF16 products of 2 M N K flops each (the FP64 product they stand for is
+    // 2 M N K); bytes: the BF16 slices in, the float2 partial sums out
+    ProfScope ps(st, KC_GEMM_OZ, 2.0 * M * N * (double)K * np,
+                 2.0 * s * ((double)M + N) * Kp + 8.0 * splits * (double)M * N);
+    k_oz_gemm<<<dim3(cdiv(N, OZ_BN), cdiv(M, OZ_BM), splits), OZ_THREADS, OZ_SMEM, st>>>(ta, tb, P);
+    KOT_LAUNCHED(1);
+  }
+  const size_t MN = (size_t)M * N;
+  const int fgrid = (int)std::min<size_t>(cdiv(MN, 256), (size_t)nsm * 8);
+  {
+    ProfScope ps(st, KC_OZ_AUX, 0.0, 8.0 * splits * (double)MN + 8.0 * (beta == 0.0 ? 1.0 : 2.0) * (double)MN);
+    k_oz_finalize<<<fgrid, 256, 0, st>>>(M, N, splits, w.w.p, w.fac.p, w.fac.p + M, beta, C, ldc, sym ? 1 : 0);
+    KOT_LAUNCHED(1);
+  }
+}
+
+int gemm_oz_error(cudaStream_t st, OzWork& w) {
+  if (!w.err.p) return 0;
+  int h = 0;
+  KOT_CUDA(cudaMemcpyAsync(&h, w.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  KOT_CUDA(cudaStreamSynchronize(st));
+  if (h) KOT_CUDA(cudaMemsetAsync(w.err.p, 0, sizeof(int), st));
+  return h;
+}
+
+void gemm_acc(cudaStream_t st, OzWork* oz, bool ta, bool tb, int M, int N, int K, double alpha,
+              const double* A, int lda, const double* B, int ldb, const double* s, double beta,
+              double* C, int ldc, int flags) {
+  if (!oz) return gemm_f64(st, ta, tb, M, N, K, alpha, A, lda, B, ldb, s, beta, C, ldc, flags);
+  // gemm_f64's op(B) is K x N; the tensor-core form takes it as N rows of K
+  gemm_oz(st, *oz, M, N, K, TcOperand{A, lda, ta, s}, TcOperand{B, ldb, !tb, nullptr}, oz->slices, alpha,
+          beta, C, ldc, (flags & G_SYM) != 0);
+}
+
+}  // namespace kot

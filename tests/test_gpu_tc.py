@@ -101,3 +101,62 @@ def test_fp64_product_is_deterministic():
         ctx.dense_product(M, N, K, 1.0, A, K, 0, B, K, 0, 0.0, Cm, N, pieces=0)
         outs.append(Cm.cpu().numpy())
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+# ---------------------------------------------------------------- FP64 emulation (pieces = -s)
+# Every row of op(A) / op(B) is cut into s fixed-point BF16 slices relative to its largest
+# magnitude; slice products of level < s are summed exactly in FP32 and combined in float-float.
+# Bound per element (slicing error 2^-(8s) of the row maximum per value, dropped levels, and the
+# float-float combination, ~2^-47 of the partial sums):
+#   |err| <= (2^(6 - 8 s) + 2^-44) K max_k|A(r,k)| max_k|B(c,k)| + FP64 rounding of the beta term.
+EMU_SHAPES = [(300, 300, 300, 0, 1, 6), (300, 300, 300, 1, 0, 6), (1, 7, 5, 0, 0, 6),
+              (257, 130, 513, 1, 0, 6), (64, 300, 97, 1, 1, 7), (513, 511, 1025, 0, 0, 6),
+              (16, 16, 1, 0, 1, 3), (1024, 1024, 1024, 0, 0, 6), (129, 257, 2100, 0, 1, 8),
+              (300, 22, 300, 1, 1, 4)]
+
+
+@pytest.mark.parametrize("M,N,K,ta,tb,s", EMU_SHAPES)
+def test_emulated_fp64_product(M, N, K, ta, tb, s):
+    rng = np.random.default_rng(11 * M + 13 * N + K + s)
+    A = rng.standard_normal((K, M) if ta else (M, K))
+    B = rng.standard_normal((K, N) if tb else (N, K))
+    # rows of very different magnitude (the slicing is relative to each row's maximum)
+    A *= np.exp2(rng.integers(-30, 30, size=(1, M) if ta else (M, 1)))
+    lda, ldb = A.shape[1], B.shape[1]
+    ctx = kot.Context(device=0)
+    C0 = rng.standard_normal((M, N))
+    Cm = torch.as_tensor(C0.copy(), device=DEV)
+    ctx.dense_product(M, N, K, -0.75, torch.as_tensor(A, device=DEV), lda, ta,
+                      torch.as_tensor(B, device=DEV), ldb, tb, 0.5, Cm, N, pieces=-s)
+    Al, Bl = op(A, ta), op(B, tb)
+    ref = -0.75 * (Al @ Bl.T) + 0.5 * C0
+    amax, bmax = np.abs(Al).max(axis=1), np.abs(Bl).max(axis=1)
+    bound = ((2.0 ** (6 - 8 * s) + 2.0 ** -44) * K * 0.75 * np.outer(amax, bmax)
+             + 4 * 2.0 ** -53 * (np.abs(ref) + 0.5 * np.abs(C0)) + 1e-300)
+    err = np.abs(Cm.cpu().numpy() - ref)
+    assert np.all(err <= bound), float((err / bound).max())
+
+
+def test_emulated_fp64_integers_are_exact():
+    # integer operands of 16 bits: two slices hold them exactly and every partial sum is an exact
+    # FP32 integer (groups of <= 512 products), so the product must equal the exact integer one;
+    # K = 2000 forces several accumulation groups per level and uneven tile edges
+    rng = np.random.default_rng(5)
+    M, N, K = 200, 190, 2000
+    A = rng.integers(-30000, 30001, size=(M, K)).astype(np.float64)
+    B = rng.integers(-30000, 30001, size=(N, K)).astype(np.float64)
+    ctx = kot.Context(device=0)
+    Cm = torch.zeros((M, N), dtype=torch.float64, device=DEV)
+    ctx.dense_product(M, N, K, 1.0, torch.as_tensor(A, device=DEV), K, 0,
+                      torch.as_tensor(B, device=DEV), K, 0, 0.0, Cm, N, pieces=-6)
+    ref = A.astype(np.int64) @ B.astype(np.int64).T          # exact (|.| < 2^53)
+    np.testing.assert_array_equal(Cm.cpu().numpy(), ref.astype(np.float64))
+
+
+def test_emulated_fp64_rejects_bad_slices():
+    ctx = kot.Context(device=0)
+    x = torch.zeros((4, 4), dtype=torch.float64, device=DEV)
+    for bad in (-1, -2, -9, 4):
+        with pytest.raises(kot.KotError) as e:
+            ctx.dense_product(4, 4, 4, 1.0, x, 4, 0, x, 4, 0, 0.0, x, 4, pieces=bad)
+        assert e.value.status == kot.ERR_INVALID
