@@ -372,6 +372,107 @@ __global__ void k_sum_partials(int nb, const double* __restrict__ partial, doubl
   if (threadIdx.x == 0) *out = s;
 }
 
+// Single-block reduction for short arrays (one launch instead of partials + sum):
+// *out = sum_i x_i y_i (y null: sum x_i^2), fixed summation order.
+__global__ void __launch_bounds__(1024) k_dot_one(size_t n, const double* __restrict__ x,
+                                                  const double* __restrict__ y, double* __restrict__ out) {
+  __shared__ double sh[1024];
+  double acc = 0.0;
+  for (size_t i = threadIdx.x; i < n; i += 1024) acc = fma(x[i], y ? y[i] : x[i], acc);
+  const double s = block_sum<1024>(acc, sh);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// One CG step on the device (single block; n is the length of the vectors): with ee = sc[5+cur],
+//   pHp = p.Hp -> sc[3];  a = ee / pHp;  x += a p;  e -= a Hp;  ee' = |e|^2 -> sc[5+(cur^1)];
+//   p = e + (ee'/ee) p.
+// pHp <= 0: nothing is updated, sc[7] = 1 and sc[5+(cur^1)] = ee.
+__global__ void __launch_bounds__(1024) k_cg_step(int n, const double* __restrict__ Hp, double* __restrict__ p,
+                                                  double* __restrict__ x, double* __restrict__ e,
+                                                  double* __restrict__ sc, int cur) {
+  __shared__ double sh[1024];
+  const int t = threadIdx.x;
+  double acc = 0.0;
+  for (int i = t; i < n; i += 1024) acc = fma(p[i], Hp[i], acc);
+  const double pHp = block_sum<1024>(acc, sh);
+  const double ee = sc[5 + cur];
+  __syncthreads();
+  if (t == 0) sc[3] = pHp;
+  if (!(pHp > 0.0)) {
+    if (t == 0) {
+      sc[7] = 1.0;
+      sc[5 + (cur ^ 1)] = ee;
+    }
+    return;
+  }
+  const double a = ee / pHp;
+  acc = 0.0;
+  for (int i = t; i < n; i += 1024) {
+    x[i] = fma(a, p[i], x[i]);
+    const double ei = fma(-a, Hp[i], e[i]);
+    e[i] = ei;
+    acc = fma(ei, ei, acc);
+  }
+  const double ee1 = block_sum<1024>(acc, sh);
+  if (t == 0) sc[5 + (cur ^ 1)] = ee1;
+  const double b = ee1 / ee;
+  for (int i = t; i < n; i += 1024) p[i] = fma(b, p[i], e[i]);
+}
+
+// Norms of the inexact-Newton test: out[0] = |x|^2 (n1 entries), out[1] = |a - b|^2 (n2 entries).
+// One block writes out directly; several blocks write partial pairs that k_sum_pairs adds.
+__global__ void k_two_norms(size_t n1, const double* __restrict__ x, size_t n2, const double* __restrict__ a,
+                            const double* __restrict__ b, double* __restrict__ out) {
+  __shared__ double sh[256];
+  double s1 = 0.0, s2 = 0.0;
+  const size_t stride = (size_t)gridDim.x * 256;
+  for (size_t i = blockIdx.x * 256 + threadIdx.x; i < n1; i += stride) s1 = fma(x[i], x[i], s1);
+  for (size_t i = blockIdx.x * 256 + threadIdx.x; i < n2; i += stride) {
+    const double d = a[i] - b[i];
+    s2 = fma(d, d, s2);
+  }
+  s1 = block_sum<256>(s1, sh);
+  __syncthreads();
+  s2 = block_sum<256>(s2, sh);
+  if (threadIdx.x == 0) {
+    out[2 * blockIdx.x] = s1;
+    out[2 * blockIdx.x + 1] = s2;
+  }
+}
+
+__global__ void k_sum_pairs(int nb, const double* __restrict__ partial, double* __restrict__ out) {
+  __shared__ double sh[256];
+  double s1 = 0.0, s2 = 0.0;
+  for (int i = threadIdx.x; i < nb; i += 256) {
+    s1 += partial[2 * i];
+    s2 += partial[2 * i + 1];
+  }
+  s1 = block_sum<256>(s1, sh);
+  __syncthreads();
+  s2 = block_sum<256>(s2, sh);
+  if (threadIdx.x == 0) {
+    out[0] = s1;
+    out[1] = s2;
+  }
+}
+
+// y = alpha A x + mu x + v  (A: n x n row-major; v may be null)
+__global__ void k_hmatvec(int n, double alpha, const double* __restrict__ A, const double* __restrict__ x,
+                          double mu, const double* __restrict__ v, double* __restrict__ y) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double* row = A + (size_t)warp * n;
+  double acc = 0.0;
+  for (int j = lane; j < n; j += 32) acc = fma(row[j], x[j], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    double r = fma(mu, x[warp], alpha * acc);
+    if (v) r += v[warp];
+    y[warp] = r;
+  }
+}
+
 __global__ void k_axpby(size_t n, double a, const double* __restrict__ x, double b,
                         const double* __restrict__ y, double* __restrict__ out) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
@@ -380,6 +481,29 @@ __global__ void k_axpby(size_t n, double a, const double* __restrict__ x, double
     if (y) v = fma(b, y[i], v);
     out[i] = v;
   }
+}
+
+// y += sgn * (num / den) x with the ratio read from device memory; den <= 0 (or NaN) leaves y
+// unchanged and sets *flag = 1 (block 0 writes it) when flag is given.
+__global__ void k_axpy_ratio(size_t n, const double* __restrict__ num, const double* __restrict__ den,
+                             double sgn, const double* __restrict__ x, double* __restrict__ y,
+                             double* __restrict__ flag) {
+  const double dn = *den;
+  if (!(dn > 0.0)) {
+    if (flag && blockIdx.x == 0 && threadIdx.x == 0) *flag = 1.0;
+    return;
+  }
+  const double a = sgn * (*num / dn);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], y[i]);
+}
+
+// y = x + (num / den) y with the ratio read from device memory
+__global__ void k_xpby_ratio(size_t n, const double* __restrict__ x, const double* __restrict__ num,
+                             const double* __restrict__ den, double* __restrict__ y) {
+  const double b = *num / *den;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = fma(b, y[i], x[i]);
 }
 
 __global__ void k_fill(size_t n, double v, double* __restrict__ out) {
@@ -535,22 +659,72 @@ void gemv_f64(cudaStream_t st, int n, double alpha, const double* A, const doubl
   KOT_CHECK_LAUNCH();
 }
 
+// Arrays up to kOneBlockN entries are reduced by one block in one launch.
+constexpr size_t kOneBlockN = 1u << 17;
+
 void dot_f64(cudaStream_t st, int n, const double* x, const double* y, double* out,
              double* partial) {
+  if ((size_t)n <= kOneBlockN) {
+    k_dot_one<<<1, 1024, 0, st>>>((size_t)n, x, y, out);
+    KOT_CHECK_LAUNCH();
+    return;
+  }
   k_dot_partial<<<kReduceBlocks, 256, 0, st>>>((size_t)n, x, y, partial);
   k_sum_partials<<<1, 256, 0, st>>>(kReduceBlocks, partial, out);
   KOT_LAUNCHED(2);
 }
 
 void sumsq_f64(cudaStream_t st, size_t n, const double* x, double* out, double* partial) {
+  if (n <= kOneBlockN) {
+    k_dot_one<<<1, 1024, 0, st>>>(n, x, nullptr, out);
+    KOT_CHECK_LAUNCH();
+    return;
+  }
   k_dot_partial<<<kReduceBlocks, 256, 0, st>>>(n, x, nullptr, partial);
   k_sum_partials<<<1, 256, 0, st>>>(kReduceBlocks, partial, out);
   KOT_LAUNCHED(2);
 }
 
+void cg_step(cudaStream_t st, int n, const double* Hp, double* p, double* x, double* e, double* sc, int cur) {
+  k_cg_step<<<1, 1024, 0, st>>>(n, Hp, p, x, e, sc, cur);
+  KOT_CHECK_LAUNCH();
+}
+
+void two_norms(cudaStream_t st, size_t n1, const double* x, size_t n2, const double* a, const double* b,
+               double* out2, double* partial) {
+  const size_t n = std::max(n1, n2);
+  if (n <= kOneBlockN / 4) {
+    k_two_norms<<<1, 256, 0, st>>>(n1, x, n2, a, b, out2);
+    KOT_CHECK_LAUNCH();
+    return;
+  }
+  const int nb = kReduceBlocks / 2;   // partial holds kReduceBlocks doubles: nb pairs
+  k_two_norms<<<nb, 256, 0, st>>>(n1, x, n2, a, b, partial);
+  k_sum_pairs<<<1, 256, 0, st>>>(nb, partial, out2);
+  KOT_LAUNCHED(2);
+}
+
+void hmatvec(cudaStream_t st, int n, double alpha, const double* A, const double* x, double mu,
+             const double* v, double* y) {
+  k_hmatvec<<<cdiv((size_t)n * 32, 256), 256, 0, st>>>(n, alpha, A, x, mu, v, y);
+  KOT_CHECK_LAUNCH();
+}
+
 void axpby(cudaStream_t st, size_t n, double a, const double* x, double b, const double* y,
            double* out) {
   k_axpby<<<std::min(cdiv(n, 256), 1216), 256, 0, st>>>(n, a, x, b, y, out);
+  KOT_CHECK_LAUNCH();
+}
+
+void axpy_ratio(cudaStream_t st, size_t n, const double* num, const double* den, double sgn,
+                const double* x, double* y, double* flag) {
+  k_axpy_ratio<<<std::min(cdiv(n, 256), 1216), 256, 0, st>>>(n, num, den, sgn, x, y, flag);
+  KOT_CHECK_LAUNCH();
+}
+
+void xpby_ratio(cudaStream_t st, size_t n, const double* x, const double* num, const double* den,
+                double* y) {
+  k_xpby_ratio<<<std::min(cdiv(n, 256), 1216), 256, 0, st>>>(n, x, num, den, y);
   KOT_CHECK_LAUNCH();
 }
 

@@ -55,25 +55,42 @@ __global__ void k_init_pad(int l, int lp, double* __restrict__ A, double* __rest
   V[(size_t)i * lp + j] = v;
 }
 
+// Order-preserving integer key of a double (-0 and +0 share the key of +0): x < y iff key(x) <
+// key(y) for non-NaN x, y.  Comparing keys costs integer instructions; FP64 compares would run
+// on this part's scarce FP64 pipe.
+__device__ __forceinline__ unsigned long long order_key(double x) {
+  const unsigned long long b = (x == 0.0) ? 0ull : (unsigned long long)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
 // rank_i = #{ j : d_j < d_i or (d_j == d_i and j < i) }  (stable ascending order); d_j is read
-// with stride `stride` from `d` (the diagonal of A: stride lp + 1).  The values are staged through
-// shared memory 256 at a time.
+// with stride `stride` from `d` (the diagonal of A: stride lp + 1).  Block (32, 8): 32 values i
+// per block, the 8 thread rows split the j range; keys are staged through shared memory.
 __global__ void k_rank_stride(int l, const double* __restrict__ d, int stride, int* __restrict__ rank) {
-  __shared__ double sh[256];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const double di = i < l ? d[(size_t)i * stride] : 0.0;
+  __shared__ unsigned long long sh[256];
+  __shared__ int cnt[8][33];
+  const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
+  const int i = blockIdx.x * 32 + tx;
+  const unsigned long long ki = i < l ? order_key(d[(size_t)i * stride]) : 0ull;
   int r = 0;
   for (int j0 = 0; j0 < l; j0 += 256) {
     __syncthreads();
-    if (j0 + (int)threadIdx.x < l) sh[threadIdx.x] = d[(size_t)(j0 + threadIdx.x) * stride];
+    if (j0 + t < l) sh[t] = order_key(d[(size_t)(j0 + t) * stride]);
     __syncthreads();
     const int n = min(256, l - j0);
-    for (int q = 0; q < n; ++q) {
-      const double dj = sh[q];
-      r += (dj < di) || (dj == di && j0 + q < i);
+    for (int q = ty; q < n; q += 8) {
+      const unsigned long long kj = sh[q];
+      r += (kj < ki) || (kj == ki && j0 + q < i);
     }
   }
-  if (i < l) rank[i] = r;
+  cnt[ty][tx] = r;
+  __syncthreads();
+  if (ty == 0 && i < l) {
+    int tot = 0;
+#pragma unroll
+    for (int y = 0; y < 8; ++y) tot += cnt[y][tx];
+    rank[i] = tot;
+  }
 }
 
 __global__ void k_gather(int l, int lp, const double* __restrict__ A, const double* __restrict__ V,
@@ -532,7 +549,7 @@ int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
     X = Xn;
     ldX = ldx;
     if (me <= kRefineDone && mr <= kRefineDone) {
-      k_rank_stride<<<cdiv(l, 256), 256, 0, st>>>(l, w.lam.p, 1, w.rank.p);
+      k_rank_stride<<<cdiv(l, 32), dim3(32, 8), 0, st>>>(l, w.lam.p, 1, w.rank.p);
       k_gather_vec<<<g2, b2, 0, st>>>(l, w.lam.p, X, ldX, w.rank.p, P, sig);
       KOT_CHECK_LAUNCH();
       KOT_LAUNCHED(2);
@@ -627,7 +644,7 @@ int jacobi_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
   if (hflags[0] == 2) throw Error{KOT_ERR_NO_CONVERGENCE, "eig: Jacobi did not converge"};
   const int sweeps = hflags[1] / 2, cur = hflags[1] & 1;
   const double* Af = cur ? A1 : A0;
-  k_rank_stride<<<cdiv(l, 256), 256, 0, st>>>(l, Af, lp + 1, w.rank.p);
+  k_rank_stride<<<cdiv(l, 32), dim3(32, 8), 0, st>>>(l, Af, lp + 1, w.rank.p);
   k_gather<<<dim3(cdiv(l, 32), cdiv(l, 8)), b2, 0, st>>>(l, lp, Af, w.V.p, w.rank.p, P, sig);
   KOT_LAUNCHED(2);
   return sweeps;

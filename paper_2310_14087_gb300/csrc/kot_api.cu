@@ -358,22 +358,22 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
       phi_star_nd(C, dgam, C->M5.p);
       t_apply(C, e, mu, C->M5.p, TPx);
       phi_nd(C, TPx, C->v5.p, C->M5.p);
-      gemv_f64(st, l, 1.0 / (2.0 * C->lambda2), C->Q.p, dgam, 0.0, Hp);
-      axpby(st, l, mu, dgam, 1.0, Hp, Hp);
-      axpby(st, l, 1.0, Hp, 1.0, C->v5.p, Hp);
+      hmatvec(st, l, 1.0 / (2.0 * C->lambda2), C->Q.p, dgam, mu, C->v5.p, Hp);
       axpby(st, l, 1.0, a1, -1.0, Hp, ev);
     }
     KOT_CUDA(cudaMemcpyAsync(pv, ev, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    int it = 0;
-    double ee = 0;
+    // CG with its step lengths kept on the device: ||e||^2 alternates between scal[5] and
+    // scal[6], p^T H p is scal[3], scal[7] flags a non-positive curvature; the host reads the
+    // norms of the stopping test (and the flag) once per iteration
+    double* sc = C->scal.p;
+    int cur = 0, it = 0;
+    fill(st, 1, 0.0, sc + 7);
+    sumsq_f64(st, l, ev, sc + 5, C->partial.p);
     while (true) {
       // stop test at the current iterate: ||e|| vs tau min(1, kappa ||r|| ||dw||)
-      sumsq_f64(st, l, ev, C->scal.p, C->partial.p);
-      sumsq_f64(st, l, dgam, C->scal.p + 1, C->partial.p);
-      axpby(st, L2, 1.0, at2, -1.0, TPx, C->M5.p);
-      sumsq_f64(st, L2, C->M5.p, C->scal.p + 2, C->partial.p);
-      fetch(C, 3);
-      ee = C->hs[0];
+      two_norms(st, l, dgam, L2, at2, TPx, sc + 1, C->partial.p);
+      fetch(C, 8);
+      const double ee = C->hs[5 + cur];
       const double enorm = std::sqrt(ee);
       if (!std::isfinite(enorm)) {
         C->force64 = false;
@@ -386,28 +386,21 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
         stop = enorm <= C->opt.tau * std::min(1.0, C->opt.kappa * r.norm * dw);
       }
       met = stop;
+      if (C->hs[7] != 0.0) {   // the last step met p^T H p <= 0 and was not taken
+        --it;
+        break;
+      }
       if (stop || it >= cap) break;
       // Hp = Q p/(2 lambda2) + mu p + Phi(T[Phi*(p)])
       phi_star_nd(C, pv, C->M5.p);
       t_apply(C, e, mu, C->M5.p, C->M6.p);
       phi_nd(C, C->M6.p, C->v5.p, C->M5.p);
-      gemv_f64(st, l, 1.0 / (2.0 * C->lambda2), C->Q.p, pv, 0.0, Hp);
-      axpby(st, l, mu, pv, 1.0, Hp, Hp);
-      axpby(st, l, 1.0, Hp, 1.0, C->v5.p, Hp);
-      dot_f64(st, l, pv, Hp, C->scal.p + 3, C->partial.p);
-      KOT_CUDA(cudaMemcpyAsync(C->hs + 3, C->scal.p + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
-      KOT_CUDA(cudaStreamSynchronize(st));
-      const double pHp = C->hs[3];
-      if (!(pHp > 0.0)) break;
-      const double a = ee / pHp;
-      axpby(st, l, 1.0, dgam, a, pv, dgam);
-      axpby(st, L2, 1.0, TPx, a, C->M6.p, TPx);
-      axpby(st, l, 1.0, ev, -a, Hp, ev);
-      sumsq_f64(st, l, ev, C->scal.p + 4, C->partial.p);
-      KOT_CUDA(cudaMemcpyAsync(C->hs + 4, C->scal.p + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
-      KOT_CUDA(cudaStreamSynchronize(st));
-      const double beta = C->hs[4] / ee;
-      axpby(st, l, 1.0, ev, beta, pv, pv);
+      hmatvec(st, l, 1.0 / (2.0 * C->lambda2), C->Q.p, pv, mu, C->v5.p, Hp);
+      // a = ||e||^2 / p^T H p: x += a p, e -= a H p, p = e + b p (one block, scalars on the
+      // device), then T[Phi*(x)] += a T[Phi*(p)]
+      cg_step(st, l, Hp, pv, dgam, ev, sc, cur);
+      axpy_ratio(st, L2, sc + 5 + cur, sc + 3, 1.0, C->M6.p, TPx, nullptr);
+      cur ^= 1;
       ++it;
     }
     total += it;

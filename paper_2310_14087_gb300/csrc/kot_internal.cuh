@@ -138,11 +138,26 @@ void dot_f64(cudaStream_t st, int n, const double* x, const double* y, double* o
 // out = sum x^2 over a n-element array
 void sumsq_f64(cudaStream_t st, size_t n, const double* x, double* out, double* partial);
 constexpr int kReduceBlocks = 128;   // size of the partial buffer the reductions need
+// One CG step with device-resident scalars (see k_cg_step in dense.cu): sc[5 + cur] = |e|^2 in,
+// sc[3] = p.Hp, sc[5 + (cur ^ 1)] = new |e|^2, sc[7] = 1 on non-positive curvature.
+void cg_step(cudaStream_t st, int n, const double* Hp, double* p, double* x, double* e, double* sc, int cur);
+// out2[0] = |x|^2 (n1 entries), out2[1] = |a - b|^2 (n2 entries); partial: kReduceBlocks doubles
+void two_norms(cudaStream_t st, size_t n1, const double* x, size_t n2, const double* a, const double* b,
+               double* out2, double* partial);
+// y = alpha A x + mu x + v (v may be null)
+void hmatvec(cudaStream_t st, int n, double alpha, const double* A, const double* x, double mu,
+             const double* v, double* y);
 
 // Elementwise helpers.
 void axpby(cudaStream_t st, size_t n, double a, const double* x, double b, const double* y,
            double* out);                                           // out = a x + b y
 void fill(cudaStream_t st, size_t n, double v, double* out);
+// Step-length updates with device-resident scalars (no host round trip inside CG):
+// y += sgn (num/den) x, or -- if den <= 0 -- nothing and *flag = 1;  y = x + (num/den) y.
+void axpy_ratio(cudaStream_t st, size_t n, const double* num, const double* den, double sgn,
+                const double* x, double* y, double* flag);
+void xpby_ratio(cudaStream_t st, size_t n, const double* x, const double* num, const double* den,
+                double* y);
 void symmetrize(cudaStream_t st, int l, double* A);                // A = (A + A^T)/2
 void add_diag(cudaStream_t st, int l, double v, double* A, int lda);
 void copy_mat(cudaStream_t st, int rows, int cols, const double* A, int lda, double* B, int ldb);
@@ -238,6 +253,11 @@ struct OzWork {
   DevBuf<float2> w;              // per-split partial sums
   DevBuf<int> err;               // set by a CTA whose bounded wait gave up
   int slices = 6;
+  // last TMA descriptors (CUtensorMap, 128 bytes) and the (buffer, rows, cols) they describe
+  alignas(64) unsigned char map_a[128], map_b[128];
+  const void* key_a = nullptr;
+  const void* key_b = nullptr;
+  int rows_a = 0, cols_a = 0, rows_b = 0, cols_b = 0;
   void release() {
     a.release();
     b.release();

@@ -42,6 +42,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "kot_internal.cuh"
 #include "tc_ptx.cuh"
@@ -63,13 +64,30 @@ constexpr int OZ_EXACT_TILES = 8;                // 8 x 64 products of |.| <= 2^
 constexpr int OZ_MAX_SLICES = 8;
 constexpr int OZ_MAX_PAIRS = OZ_MAX_SLICES * (OZ_MAX_SLICES + 1) / 2;
 constexpr int OZ_MAX_SPLITS = 8;
+constexpr int kSplitRows = 16;        // thread rows of a cluster slicing block (32 x 16 threads)
 constexpr int kOzClusterK = 8 * 64;   // K up to which one (portable, <= 8 block) cluster spans a row
 
 inline int cdiv(size_t a, int b) { return (int)((a + b - 1) / b); }
 
+static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+
+// SM count of the current device, queried once per device
+int sm_count() {
+  static int cache[64] = {};
+  int dev = 0;
+  KOT_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) throw Error{KOT_ERR_CUDA, "device ordinal out of range"};
+  if (cache[dev] == 0) {
+    int n = 0;
+    KOT_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
 struct OzPlan {
   int M, N, Kp, nk, npairs;
-  int pbeg[OZ_MAX_SPLITS + 1];        // split z takes slice pairs [pbeg[z], pbeg[z + 1])
+  int sbeg[OZ_MAX_SPLITS + 1];        // split z takes tile steps [sbeg[z], sbeg[z + 1])
   signed char pa[OZ_MAX_PAIRS], pb[OZ_MAX_PAIRS], lv[OZ_MAX_PAIRS];
   float2* W;                          // splits x M x N partial sums (hi, lo)
   int* err;
@@ -105,8 +123,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * OZ_BM, n0 = blockIdx.x * OZ_BN, z = blockIdx.z;
-  const int p0 = P.pbeg[z], p1 = P.pbeg[z + 1];
   const int nk = P.nk;
+  // split z takes the tile steps [s0, s1) of the sequence (pair p, k tile kt), step = p nk + kt
+  const int s0 = P.sbeg[z], s1 = P.sbeg[z + 1];
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < OZ_STAGES; ++s) {
@@ -129,21 +148,26 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 
   if (warp == 4) {
     if (lane == 0) {
-      // TMA producer: the tiles of every slice pair of this split, in order
-      int n = 0;
-      for (int p = p0; p < p1 && ok; ++p) {
-        const int xa = P.pa[p] * P.Kp, xb = P.pb[p] * P.Kp;
-        for (int kt = 0; kt < nk; ++kt, ++n) {
-          const int s = n % OZ_STAGES;
-          const uint32_t ph = (uint32_t)(n / OZ_STAGES) & 1u;
-          if (!mbar_wait(&empty[s], ph ^ 1u)) {
-            ok = false;
-            break;
-          }
-          mbar_expect_tx(&full[s], OZ_STAGE);
-          uint8_t* st = smem + s * OZ_STAGE;
-          tma_load_2d(st, &ta, &full[s], xa + kt * OZ_BK, m0);
-          tma_load_2d(st + OZ_A_BYTES, &tb, &full[s], xb + kt * OZ_BK, n0);
+      // TMA producer: the tiles of this split's steps, in order (counters kept incrementally:
+      // this thread is on the critical path)
+      int p = s0 / nk, kt = s0 - p * nk, s = 0;
+      uint32_t ph = 0;
+      for (int n = s0; n < s1; ++n) {
+        if (!mbar_wait(&empty[s], ph ^ 1u)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&full[s], OZ_STAGE);
+        uint8_t* st = smem + s * OZ_STAGE;
+        tma_load_2d(st, &ta, &full[s], P.pa[p] * P.Kp + kt * OZ_BK, m0);
+        tma_load_2d(st + OZ_A_BYTES, &tb, &full[s], P.pb[p] * P.Kp + kt * OZ_BK, n0);
+        if (++kt == nk) {
+          kt = 0;
+          ++p;
+        }
+        if (++s == OZ_STAGES) {
+          s = 0;
+          ph ^= 1u;
         }
       }
     }
@@ -151,38 +175,44 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     if (lane == 0) {
       // MMA issuer
       constexpr uint32_t idesc = idesc_bf16(OZ_BM, OZ_BN);
-      int n = 0, g = -1, gt = 0, prev = -1;
-      for (int p = p0; p < p1 && ok; ++p) {
+      int g = -1, gt = 0, prev = -1;
+      int p = s0 / nk, kt = s0 - p * nk, s = 0;
+      uint32_t ph = 0;
+      for (int n = s0; n < s1; ++n) {
         const int lv = P.lv[p];
-        for (int kt = 0; kt < nk; ++kt, ++n) {
-          const bool first = oz_new_group(prev, lv, gt);
-          if (first) {
-            if (g >= 0) umma_commit(&acc_full[g & 1]);
-            ++g;
-            gt = 0;
-            // the buffer must have been read out (group g - 2) before it is overwritten
-            if (!mbar_wait(&acc_empty[g & 1], (((uint32_t)g >> 1) & 1u) ^ 1u)) {
-              ok = false;
-              break;
-            }
-          }
-          const int s = n % OZ_STAGES;
-          const uint32_t ph = (uint32_t)(n / OZ_STAGES) & 1u;
-          if (!mbar_wait(&full[s], ph)) {
+        const bool first = oz_new_group(prev, lv, gt);
+        if (first) {
+          if (g >= 0) umma_commit(&acc_full[g & 1]);
+          ++g;
+          gt = 0;
+          // the buffer must have been read out (group g - 2) before it is overwritten
+          if (!mbar_wait(&acc_empty[g & 1], (((uint32_t)g >> 1) & 1u) ^ 1u)) {
             ok = false;
             break;
           }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t a_addr = smem_u32(smem + s * OZ_STAGE);
-          const uint32_t b_addr = a_addr + OZ_A_BYTES;
-          const uint32_t d = tmem + (uint32_t)((g & 1) * OZ_BN);
+        }
+        if (!mbar_wait(&full[s], ph)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a_addr = smem_u32(smem + s * OZ_STAGE);
+        const uint32_t b_addr = a_addr + OZ_A_BYTES;
+        const uint32_t d = tmem + (uint32_t)((g & 1) * OZ_BN);
 #pragma unroll
-          for (int k = 0; k < OZ_BK / 16; ++k)
-            umma_bf16(d, smem_desc_sw128(a_addr + 32 * k), smem_desc_sw128(b_addr + 32 * k), idesc,
-                      (first && k == 0) ? 0u : 1u);
-          umma_commit(&empty[s]);
-          ++gt;
-          prev = lv;
+        for (int k = 0; k < OZ_BK / 16; ++k)
+          umma_bf16(d, smem_desc_sw128(a_addr + 32 * k), smem_desc_sw128(b_addr + 32 * k), idesc,
+                    (first && k == 0) ? 0u : 1u);
+        umma_commit(&empty[s]);
+        ++gt;
+        prev = lv;
+        if (++kt == nk) {
+          kt = 0;
+          ++p;
+        }
+        if (++s == OZ_STAGES) {
+          s = 0;
+          ph ^= 1u;
         }
       }
       if (g >= 0 && ok) umma_commit(&acc_full[g & 1]);
@@ -194,16 +224,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // epilogue warps 0-3: warp w owns accumulator lanes (output rows) 32 w .. 32 w + 31
     int G = 0;
     {
-      int gt = 0, prev = -1;
-      for (int p = p0; p < p1; ++p) {
+      int gt = 0, prev = -1, p = s0 / nk, kt = s0 - p * nk;
+      for (int n = s0; n < s1; ++n) {
         const int lv = P.lv[p];
-        for (int kt = 0; kt < nk; ++kt) {
-          if (oz_new_group(prev, lv, gt)) {
-            ++G;
-            gt = 0;
-          }
-          ++gt;
-          prev = lv;
+        if (oz_new_group(prev, lv, gt)) {
+          ++G;
+          gt = 0;
+        }
+        ++gt;
+        prev = lv;
+        if (++kt == nk) {
+          kt = 0;
+          ++p;
         }
       }
     }
@@ -228,12 +260,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[g & 1]);
     }
-    const int row = m0 + warp * 32 + lane;
-    if (ok && row < P.M) {
-      float2* wr = P.W + ((size_t)z * P.M + row) * P.N;
+    if (ok) {
+      // Every MMA has completed (the last group's commit covers them), so the operand ring is
+      // free: each warp stages its 32 x 64 (hi, lo) block there and writes it back row by row,
+      // 32 consecutive columns per store instruction.
+      float2* buf = (float2*)(smem + (size_t)warp * 32 * (OZ_BN + 1) * sizeof(float2));
 #pragma unroll
-      for (int j = 0; j < OZ_BN; ++j)
-        if (n0 + j < P.N) wr[n0 + j] = make_float2(hi[j], lo[j]);
+      for (int j = 0; j < OZ_BN; ++j) buf[lane * (OZ_BN + 1) + j] = make_float2(hi[j], lo[j]);
+      __syncwarp();
+      const int rbase = m0 + warp * 32;
+      for (int rr = 0; rr < 32; ++rr) {
+        const int row = rbase + rr;
+        if (row >= P.M) break;
+        float2* wr = P.W + ((size_t)z * P.M + row) * P.N;
+#pragma unroll
+        for (int h = 0; h < OZ_BN / 32; ++h) {
+          const int col = n0 + 32 * h + lane;
+          if (col < P.N) wr[col] = buf[rr * (OZ_BN + 1) + 32 * h + lane];
+        }
+      }
     }
   }
   if (!ok) atomicExch(P.err, 1);
@@ -396,25 +441,25 @@ __global__ void k_oz_split(OzSplitArgs a) {
 // per-row maximum exponents, reads its peers' through distributed shared memory, and slices its
 // own values (no second pass over the operand, no second launch).  All blocks of a cluster share
 // blockIdx.y and blockIdx.z, so a cluster is either wholly inside the operand or wholly outside.
-__global__ void k_oz_split_cluster(OzSplitArgs a) {
+__global__ void __launch_bounds__(32 * kSplitRows) k_oz_split_cluster(OzSplitArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   const OzOperand& o = a.op[blockIdx.z];
   const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
   if (r0 >= o.rows) return;
-  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x kSplitRows
   const int s = a.s, Kp = a.Kp;
   __shared__ double tile[32][65];                 // [row][k - k0]
   __shared__ int pmax[32], se[32];
   if (o.trans) {
     const int r = r0 + tx;
 #pragma unroll
-    for (int kk = ty; kk < 64; kk += 8) {
+    for (int kk = ty; kk < 64; kk += kSplitRows) {
       const int k = k0 + kk;
       tile[tx][kk] = (k < o.K && r < o.rows) ? oz_load(o, r, k) : 0.0;
     }
   } else {
 #pragma unroll
-    for (int i = ty; i < 32; i += 8) {
+    for (int i = ty; i < 32; i += kSplitRows) {
       const int r = r0 + i;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -425,7 +470,7 @@ __global__ void k_oz_split_cluster(OzSplitArgs a) {
   }
   __syncthreads();
 #pragma unroll
-  for (int i = ty; i < 32; i += 8) {
+  for (int i = ty; i < 32; i += kSplitRows) {
     int e = max(biased_exp(tile[i][tx]), biased_exp(tile[i][tx + 32]));
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, off));
@@ -443,7 +488,7 @@ __global__ void k_oz_split_cluster(OzSplitArgs a) {
   cluster.sync();   // peers are done reading pmax; se is visible block-wide
   const size_t rowlen = (size_t)s * Kp;
 #pragma unroll
-  for (int i = ty; i < 32; i += 8) {
+  for (int i = ty; i < 32; i += kSplitRows) {
     const int r = r0 + i;
     if (r >= o.rows) continue;
 #pragma unroll
@@ -465,13 +510,17 @@ __global__ void k_oz_split_cluster(OzSplitArgs a) {
 
 // ------------------------------------------------------------------ finalize
 __device__ __forceinline__ double oz_value(const float2* __restrict__ W, size_t MN, int splits, size_t idx) {
-  float2 w = W[idx];
-  float hi = w.x, lo = w.y;
-  for (int z = 1; z < splits; ++z) {
-    const float2 u = W[(size_t)z * MN + idx];
-    ff_add(hi, lo, u.x);
-    lo = __fadd_rn(lo, u.y);
-  }
+  float2 u[OZ_MAX_SPLITS];
+#pragma unroll
+  for (int z = 0; z < OZ_MAX_SPLITS; ++z)
+    if (z < splits) u[z] = __ldcs(W + (size_t)z * MN + idx);   // all loads in flight at once
+  float hi = u[0].x, lo = u[0].y;
+#pragma unroll
+  for (int z = 1; z < OZ_MAX_SPLITS; ++z)
+    if (z < splits) {
+      ff_add(hi, lo, u[z].x);
+      lo = __fadd_rn(lo, u[z].y);
+    }
   return (double)hi + (double)lo;
 }
 
@@ -510,9 +559,7 @@ void gemm_oz(cudaStream_t st, OzWork& w, int M, int N, int K, const TcOperand& A
   const int s = slices;
   const int Kp = cdiv(K, OZ_BK) * OZ_BK;
   const int nkb = cdiv(K, 64);
-  int dev = 0, nsm = 0;
-  KOT_CUDA(cudaGetDevice(&dev));
-  KOT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int nsm = sm_count();
 
   OzPlan P;
   P.M = M;
@@ -529,8 +576,9 @@ void gemm_oz(cudaStream_t st, OzWork& w, int M, int N, int K, const TcOperand& A
     }
   P.npairs = np;
   const int tiles = cdiv(N, OZ_BN) * cdiv(M, OZ_BM);
-  const int splits = std::max(1, std::min({OZ_MAX_SPLITS, np, nsm / tiles}));
-  for (int z = 0; z <= splits; ++z) P.pbeg[z] = z * np / splits;
+  const int splits = std::max(1, std::min({OZ_MAX_SPLITS, np * (Kp / OZ_BK), nsm / tiles}));
+  const int T = np * P.nk;   // tile steps (pair, k tile) of one output tile
+  for (int z = 0; z <= splits; ++z) P.sbeg[z] = (int)((long long)z * T / splits);
 
   w.a.alloc((size_t)M * s * Kp);
   w.b.alloc((size_t)N * s * Kp);
@@ -570,7 +618,7 @@ void gemm_oz(cudaStream_t st, OzWork& w, int M, int N, int K, const TcOperand& A
     if (K <= kOzClusterK) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(nkb, rb, 2);
-      cfg.blockDim = bs;
+      cfg.blockDim = dim3(32, kSplitRows);
       cfg.dynamicSmemBytes = 0;
       cfg.stream = st;
       cudaLaunchAttribute attr[1];
@@ -589,8 +637,24 @@ void gemm_oz(cudaStream_t st, OzWork& w, int M, int N, int K, const TcOperand& A
     }
   }
 
-  const CUtensorMap ta = make_bf16_map(w.a.p, M, s * Kp, OZ_BM);
-  const CUtensorMap tb = make_bf16_map(w.b.p, N, s * Kp, OZ_BN);
+  // descriptors are re-encoded only when the slice buffers or their shapes change
+  if (w.key_a != w.a.p || w.rows_a != M || w.cols_a != s * Kp) {
+    const CUtensorMap m = make_bf16_map(w.a.p, M, s * Kp, OZ_BM);
+    std::memcpy(w.map_a, &m, sizeof(m));
+    w.key_a = w.a.p;
+    w.rows_a = M;
+    w.cols_a = s * Kp;
+  }
+  if (w.key_b != w.b.p || w.rows_b != N || w.cols_b != s * Kp) {
+    const CUtensorMap m = make_bf16_map(w.b.p, N, s * Kp, OZ_BN);
+    std::memcpy(w.map_b, &m, sizeof(m));
+    w.key_b = w.b.p;
+    w.rows_b = N;
+    w.cols_b = s * Kp;
+  }
+  CUtensorMap ta, tb;
+  std::memcpy(&ta, w.map_a, sizeof(ta));
+  std::memcpy(&tb, w.map_b, sizeof(tb));
   static bool attr_set = false;
   if (!attr_set) {
     KOT_CUDA(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
