@@ -160,6 +160,10 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true", help="do not time the host-buffer path")
     ap.add_argument("--profile", default="roofline", choices=["roofline", "all", "none"],
                     help="kernel classes timed with CUDA events inside the timed region")
+    ap.add_argument("--method", default="ssn", choices=["ssn", "eg"],
+                    help="ssn: Algorithm 2 (the headline); eg: the pure extragradient method of "
+                         "App. F, a fixed number of steps per problem")
+    ap.add_argument("--eg-steps", type=int, default=200, help="EG steps per problem (--method eg)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -176,6 +180,8 @@ def main():
     dev = f"cuda:{local_rank}"
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device(dev))
+    if args.method == "eg":
+        return eg_bench(args, world, rank, local_rank, dev)
     p = make_problem(args.workload, rank, 0)
     probs = [make_problem(args.workload, rank, k) for k in range(args.steps)]
     dprobs = [kot.DeviceProblem.from_problem(q, dev) for q in probs]
@@ -257,6 +263,62 @@ def main():
         report(args, probs, world, ms_max, ms_local, stats, launches, iters, conv, clocks, peaks,
                None if args.skip_other else (other_prec, o_value, o_ms_max, o_iters, o_conv), e2e,
                float(conv_all.item()))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def eg_bench(args, world, rank, local_rank, dev):
+    """Pure extragradient (App. F, Fig. 6): --eg-steps steps per problem after the features;
+    reports EG steps per second and the residual reached, beside the SSN time to 1e-6."""
+    import torch
+    import torch.distributed as dist
+    from paper_2310_14087_gb300 import kot
+    prec = kot.MIXED if args.precision == "mixed" else kot.FP64
+    stream = torch.cuda.Stream(device=dev)
+    ctx = kot.Context(device=local_rank, stream=stream.cuda_stream, precision=prec,
+                      max_iter=args.eg_steps)
+    probs = [kot.DeviceProblem.from_problem(make_problem(args.workload, rank, k), dev)
+             for k in range(args.steps)]
+    warm = [kot.DeviceProblem.from_problem(make_problem(args.workload, rank, -1 - k), dev)
+            for k in range(args.warmup)]
+    l = WORKLOADS[args.workload]["l"]
+    g = torch.zeros(l, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(dp):
+        ctx.build_features(dp.X, dp.Y, dp.Xf, dp.Yf, dp.sigma, dp.lambda1, dp.lambda2)
+        return ctx.eg_solve(1e-30, g, allow_no_convergence=True)
+
+    for dp in warm:
+        step(dp)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, resid = 0.0, []
+    for dp in probs:
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        r = step(dp)
+        with torch.cuda.stream(stream):
+            b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+        resid.append(r.residual)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    if rank == 0:
+        total = args.steps * args.eg_steps * world
+        print(json.dumps({
+            "metric": "pure extragradient steps/s (App. F), features included", "method": "eg",
+            "value": total / (float(t.item()) / 1e3), "unit": "EG steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(t.item()) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, **config_of(args.workload), "precision": args.precision,
+                       "eg_steps_per_problem": args.eg_steps, "eg_step_size": "1/L",
+                       "residual_after_steps": resid}}), flush=True)
     if world > 1:
         dist.destroy_process_group()
 

@@ -153,6 +153,14 @@ kot_status kot_newton_direction(kot_ctx* ctx, const double* gamma, const double*
 kot_status kot_ssn_solve(kot_ctx* ctx, double tol, double* gamma_out, double* X_out,
                          const double* gamma0, const double* X0, kot_result* res);
 
+/* The pure extragradient method (the comparison method of App. F, Fig. 6): from v0 = (gamma0, X0)
+ * (NULL = zeros), v_{k+1} = EG(v_k) -- the projected extragradient step of Algorithm 2's
+ * safeguard, with step opt.eg_step (<= 0: 1/L) -- until ||R(v_k)|| <= tol or opt.max_iter steps.
+ * Outputs and history as for kot_ssn_solve (iters = eg_taken = steps; the history holds
+ * ||R(v_k)||).  Returns KOT_ERR_NO_CONVERGENCE at the cap with the last iterate in the outputs. */
+kot_status kot_eg_solve(kot_ctx* ctx, double tol, double* gamma_out, double* X_out,
+                        const double* gamma0, const double* X0, kot_result* res);
+
 /* Residual history of the last solve (record_history = 1): copies min(cap, iters + 1) values
  * of ||R(w_k)|| to the host array hist; *count receives the number copied. */
 kot_status kot_get_history(kot_ctx* ctx, double* hist, int cap, int* count);
@@ -163,6 +171,17 @@ kot_status kot_get_history(kot_ctx* ctx, double* hist, int cap, int* count);
  * FP64 CG steps)} into the host array out (5 * cap doubles);
  * *count receives the number of rows. */
 kot_status kot_get_trace(kot_ctx* ctx, double* out, int cap, int* count);
+
+/* Potentials and transport map from dual weights gamma (l), at m query points (m x d):
+ * stationarity of the Lagrangian of Eq. (3.2) gives the empirical Kantorovich potentials
+ *   u(x) = (w_mu(x) - sum_i gamma_i k(xf_i, x)) / (2 lambda2),  w_mu(x) = (1/n) sum_j k(x_j, x)
+ * (side 0; side 1: v(y) with the y samples and yf), so that averaging u over the x samples plus v
+ * over the y samples gives OT-hat (Sec. 3).  Outputs (any may be NULL, not all): u (m), grad (m x d)
+ * = grad u, tmap (m x d) = x - grad u(x), the map estimate for the cost ||x - y||^2/2 used for
+ * Figs. 1, 4 and 7.  Needs the samples of kot_build_features (KOT_ERR_STATE after
+ * kot_set_features).  Pointers follow the context's pointer mode. */
+kot_status kot_potentials(kot_ctx* ctx, int side, int m, const double* points, const double* gamma,
+                          double* u, double* grad, double* tmap);
 
 /* One problem of a batch.  Arrays follow the context's pointer mode. */
 typedef struct {

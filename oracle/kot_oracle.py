@@ -357,6 +357,31 @@ def newton_direction(F: Features, res: Residual, mu: float, opt: Options,
 
 
 # ----------------------------------------------------------------------------------------
+# Potentials and transport map from the dual solution
+# ----------------------------------------------------------------------------------------
+def potential(S: np.ndarray, Sf: np.ndarray, gamma: np.ndarray, sigma: float, lambda2: float,
+              P: np.ndarray):
+    """Empirical Kantorovich potential of one side and its gradient at the points P (m x d).
+
+    Stationarity of the Lagrangian of Eq. (3.2) in u gives
+        u(x) = (w_mu(x) - sum_i gamma_i k(xf_i, x)) / (2 lambda2),  w_mu(x) = (1/n) sum_j k(x_j, x),
+    (the same with Y, yf for v); with k(a, x) = exp(-||a - x||^2 / (2 sigma^2)),
+        grad u(x) = (1/(2 lambda2)) sum_a c_a k(a, x) (a - x) / sigma^2,
+    c_a = 1/n for the samples a = x_j and -gamma_i for the filling points a = xf_i.  The map
+    estimate for the cost ||x - y||^2 / 2 is T(x) = x - grad u(x) (the displacement of Figs. 1,
+    4 and 7).  Returns (u (m), grad (m x d), T (m x d)).  Pinned by the estimator identity
+    <u, w_mu> + <v, w_nu> = OT-hat (Sec. 3), by finite differences and by gamma = 0."""
+    n = S.shape[0]
+    A = np.vstack([S, Sf])                                   # sources a
+    c = np.concatenate([np.full(n, 1.0 / n), -np.asarray(gamma, dtype=np.float64)])
+    Kx = gaussian_kernel(P, A, sigma)                        # m x (n + l)
+    W = Kx * c[None, :]
+    u = W.sum(axis=1) / (2.0 * lambda2)
+    grad = (W @ A - W.sum(axis=1)[:, None] * P) / (2.0 * lambda2 * sigma * sigma)
+    return u, grad, P - grad
+
+
+# ----------------------------------------------------------------------------------------
 # Extragradient on the min-max problem Eq. (4.1), used as the safeguard of Algorithm 2
 # ----------------------------------------------------------------------------------------
 def eg_lipschitz(F: Features) -> float:

@@ -42,6 +42,73 @@ __global__ void k_embed(int n, int d, const double* __restrict__ S, const double
   if (t == 0) w[i] = red[0] / (double)n;
 }
 
+// Potential and gradient at query point x_q (one CTA per point):
+//   u = (1/(2 l2)) sum_a c_a k(a, x),  grad = (1/(2 l2 sigma^2)) sum_a c_a k(a, x) (a - x),
+// over the sources a = S_j (c = 1/n) then Sf_i (c = -gamma_i).  Sources are taken 256 at a
+// time: each thread forms one weight c_a k(a, x) in shared memory, then thread c < d adds up
+// coordinate c of the tile's weighted sources (coalesced rows); all sums in a fixed order.
+__global__ void k_potential(int m, int d, int n, const double* __restrict__ S, int l,
+                            const double* __restrict__ Sf, const double* __restrict__ gamma,
+                            const double* __restrict__ Pq, double inv2s2, double scale_u,
+                            double scale_g, double* __restrict__ u, double* __restrict__ grad,
+                            double* __restrict__ tmap) {
+  extern __shared__ double sh[];          // x (d), weights (256), reduction (256), coordinate sums (d)
+  double* x = sh;
+  double* wt = sh + d;
+  double* red = wt + 256;
+  double* g1 = red + 256;
+  const int q = blockIdx.x, t = threadIdx.x;
+  for (int c = t; c < d; c += 256) {
+    x[c] = Pq[(size_t)q * d + c];
+    g1[c] = 0.0;
+  }
+  __syncthreads();
+  double s0 = 0.0;
+  const int total = n + l;
+  for (int a0 = 0; a0 < total; a0 += 256) {
+    const int a = a0 + t;
+    double w = 0.0;
+    if (a < total) {
+      const double* src = a < n ? S + (size_t)a * d : Sf + (size_t)(a - n) * d;
+      double dist = 0.0;
+      for (int c = 0; c < d; ++c) {
+        const double diff = src[c] - x[c];
+        dist = fma(diff, diff, dist);
+      }
+      w = (a < n ? 1.0 / (double)n : -gamma[a - n]) * exp(-dist * inv2s2);
+    }
+    wt[t] = w;
+    s0 += w;
+    __syncthreads();
+    if (grad || tmap) {
+      const int cnt = min(256, total - a0);
+      for (int c = t; c < d; c += 256) {
+        double acc = g1[c];
+        for (int b = 0; b < cnt; ++b) {
+          const int ab = a0 + b;
+          const double* src = ab < n ? S + (size_t)ab * d : Sf + (size_t)(ab - n) * d;
+          acc = fma(wt[b], src[c], acc);
+        }
+        g1[c] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  red[t] = s0;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (t < o) red[t] += red[t + o];
+    __syncthreads();
+  }
+  const double S0 = red[0];
+  if (t == 0 && u) u[q] = scale_u * S0;
+  for (int c = t; c < d; c += 256) {
+    const double gc = scale_g * (g1[c] - S0 * x[c]);
+    if (grad) grad[(size_t)q * d + c] = gc;
+    if (tmap) tmap[(size_t)q * d + c] = x[c] - gc;
+  }
+}
+
 // Pair sums over 64 x 64 tiles (I, J) of the n x n kernel matrix, J >= I; off-diagonal tiles
 // count twice.  partial[I * nb + J] receives the tile's weighted sum (zero for J < I).
 constexpr int PT = 64;
@@ -231,6 +298,20 @@ void embed_f64(cudaStream_t st, int n, int d, int l, const double* S, const doub
   if (smem > 48 * 1024) KOT_CUDA(cudaFuncSetAttribute(k_embed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ProfScope ps(st, KC_EMBED, (double)n * l * (3.0 * d + 2.0), 8.0 * ((double)n * d + (double)l * d + l));
   k_embed<<<l, 256, smem, st>>>(n, d, S, P, inv2s2, w);
+  KOT_CHECK_LAUNCH();
+}
+
+void potential_f64(cudaStream_t st, int m, int d, int n, const double* S, int l, const double* Sf,
+                   const double* gamma, const double* Pq, double sigma, double lambda2, double* u,
+                   double* grad, double* tmap) {
+  if (m <= 0) return;
+  const size_t smem = (size_t)(2 * d + 512) * sizeof(double);
+  if (smem > 48 * 1024)
+    KOT_CUDA(cudaFuncSetAttribute(k_potential, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const double inv2s2 = 1.0 / (2.0 * sigma * sigma);
+  const double scale_u = 1.0 / (2.0 * lambda2), scale_g = 1.0 / (2.0 * lambda2 * sigma * sigma);
+  ProfScope ps(st, KC_EMBED, (double)m * (n + l) * (5.0 * d + 4.0), 8.0 * ((double)(n + l + 2 * m) * d + l));
+  k_potential<<<m, 256, smem, st>>>(m, d, n, S, l, Sf, gamma, Pq, inv2s2, scale_u, scale_g, u, grad, tmap);
   KOT_CHECK_LAUNCH();
 }
 

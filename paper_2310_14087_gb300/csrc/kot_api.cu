@@ -54,6 +54,11 @@ struct kot_ctx {
   bool have = false;
   double lambda1 = 0, lambda2 = 0, q2 = 0, eps = 0, eg_L = 0;
   DevBuf<double> Q, K, R, z, w_mu, w_nu, c;
+  // samples and filling points of the last kot_build_features (for kot_potentials)
+  DevBuf<double> sX, sY, sXf, sYf;
+  int d = 0, n = 0;
+  double sigma = 0;
+  bool have_samples = false;
   DevBuf<double> stage[8];                     // host-pointer mode staging
   DevBuf<double> g, X, vg, vX, tg, tX, dg, dX;
   ResState rw, rv, rt;
@@ -592,7 +597,8 @@ kot_status kot_destroy(kot_ctx* C) {
                             &C->M3, &C->M4, &C->M5, &C->M6, &C->TU, &C->TV, &C->TW, &C->TG,
                             &C->v1, &C->v2, &C->v3, &C->v4, &C->v5, &C->v6, &C->partial,
                             &C->scal, &C->bounds, &C->rw.r1, &C->rw.r2, &C->rv.r1, &C->rv.r2,
-                            &C->rt.r1, &C->rt.r2, &C->eZ, &C->eP, &C->esig})
+                            &C->rt.r1, &C->rt.r2, &C->eZ, &C->eP, &C->esig, &C->sX, &C->sY,
+                            &C->sXf, &C->sYf})
     b->release();
   C->jw.release();
   C->tc.a.release();
@@ -627,6 +633,7 @@ kot_status kot_build_features(kot_ctx* C, int d, int n, const double* X, const d
   return run(C, [&] {
     KOT_CUDA(cudaSetDevice(C->opt.device));
     C->have = false;
+    C->have_samples = false;
     C->l = l;
     ensure(C, l);
     reset_slots(C);
@@ -650,6 +657,19 @@ kot_status kot_build_features(kot_ctx* C, int d, int n, const double* X, const d
     C->lambda2 = lambda2;
     factor(C);
     compute_eg_L(C);
+    C->sX.alloc((size_t)n * d);
+    C->sY.alloc((size_t)n * d);
+    C->sXf.alloc((size_t)l * d);
+    C->sYf.alloc((size_t)l * d);
+    KOT_CUDA(cudaMemcpyAsync(C->sX.p, dX, (size_t)n * d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    KOT_CUDA(cudaMemcpyAsync(C->sY.p, dY, (size_t)n * d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    KOT_CUDA(cudaMemcpyAsync(C->sXf.p, dXf, (size_t)l * d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    KOT_CUDA(cudaMemcpyAsync(C->sYf.p, dYf, (size_t)l * d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    KOT_CUDA(cudaStreamSynchronize(st));
+    C->d = d;
+    C->n = n;
+    C->sigma = sigma;
+    C->have_samples = true;
     C->have = true;
   });
 }
@@ -665,6 +685,7 @@ kot_status kot_set_features(kot_ctx* C, int l, const double* Q, const double* z,
   return run(C, [&] {
     KOT_CUDA(cudaSetDevice(C->opt.device));
     C->have = false;
+    C->have_samples = false;
     C->l = l;
     ensure(C, l);
     reset_slots(C);
@@ -916,6 +937,117 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
   R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (res) *res = R;
   return s;
+}
+
+kot_status kot_eg_solve(kot_ctx* C, double tol, double* gamma_out, double* X_out, const double* gamma0,
+                        const double* X0, kot_result* res) {
+  if (!C) return KOT_ERR_INVALID;
+  if (!gamma_out || !pos_finite(tol)) {
+    C->err = "kot_eg_solve: invalid argument";
+    return KOT_ERR_INVALID;
+  }
+  if (!C->have) {
+    C->err = "kot_eg_solve: no features";
+    return KOT_ERR_STATE;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  kot_result R{};
+  bool converged = false;
+  kot_status s = run(C, [&] {
+    KOT_CUDA(cudaSetDevice(C->opt.device));
+    const int l = C->l;
+    const size_t L2 = (size_t)l * l;
+    cudaStream_t st = C->st;
+    const kot_options& o = C->opt;
+    reset_slots(C);
+    C->eig_calls = C->eig_sweeps = C->eig_refined = C->eig_refine_steps = 0;
+    if (gamma0) {
+      const double* p = dev_in(C, 0, gamma0, l);
+      KOT_CUDA(cudaMemcpyAsync(C->vg.p, p, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+      fill(st, l, 0.0, C->vg.p);
+    }
+    if (X0) {
+      const double* p = dev_in(C, 1, X0, L2);
+      KOT_CUDA(cudaMemcpyAsync(C->vX.p, p, L2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+      fill(st, L2, 0.0, C->vX.p);
+    }
+    const double eta = o.eg_step > 0 ? o.eg_step : 1.0 / C->eg_L;
+    residual(C, C->vg.p, C->vX.p, C->ev, nullptr, C->rv);
+    C->hist.clear();
+    C->trace.clear();
+    if (o.record_history) C->hist.push_back(C->rv.norm);
+    int it = 0;
+    while (C->rv.norm > tol && it < o.max_iter) {
+      eg_step(C, eta);
+      residual(C, C->vg.p, C->vX.p, C->ev, &C->ev, C->rv);
+      ++it;
+      if (o.record_history) C->hist.push_back(C->rv.norm);
+    }
+    converged = C->rv.norm <= tol;
+    double ot = 0;
+    const double obj = objective_and_ot(C, C->vg.p, &ot);
+    dev_out(C, gamma_out, C->vg.p, l);
+    dev_out(C, X_out, C->vX.p, L2);
+    KOT_CUDA(cudaStreamSynchronize(st));
+    R.iters = it;
+    R.eg_taken = it;
+    R.residual = C->rv.norm;
+    R.r1_norm = C->rv.n1;
+    R.r2_norm = C->rv.n2;
+    R.objective = obj;
+    R.ot_hat = ot;
+    R.eps = C->eps;
+    R.eig_calls = (int)C->eig_calls;
+    R.eig_sweeps = (int)C->eig_sweeps;
+    R.eig_refined = (int)C->eig_refined;
+    R.eig_refine_steps = (int)C->eig_refine_steps;
+  });
+  if (s == KOT_OK && !converged) {
+    s = KOT_ERR_NO_CONVERGENCE;
+    C->err = "kot_eg_solve: iteration cap reached";
+  }
+  R.status = s;
+  R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (res) *res = R;
+  return s;
+}
+
+kot_status kot_potentials(kot_ctx* C, int side, int m, const double* points, const double* gamma,
+                          double* u, double* grad, double* tmap) {
+  if (!C) return KOT_ERR_INVALID;
+  if ((side != 0 && side != 1) || m < 1 || !points || !gamma || (!u && !grad && !tmap)) {
+    C->err = "kot_potentials: invalid argument";
+    return KOT_ERR_INVALID;
+  }
+  if (!C->have || !C->have_samples) {
+    C->err = "kot_potentials: needs the samples of kot_build_features";
+    return KOT_ERR_STATE;
+  }
+  return run(C, [&] {
+    KOT_CUDA(cudaSetDevice(C->opt.device));
+    const int d = C->d, l = C->l;
+    const double* dP = dev_in(C, 0, points, (size_t)m * d);
+    const double* dg = dev_in(C, 1, gamma, (size_t)l);
+    double *du = u, *dgr = grad, *dt = tmap;
+    if (C->opt.host_pointers) {
+      C->stage[2].alloc((size_t)m);
+      C->stage[3].alloc((size_t)m * d);
+      C->stage[4].alloc((size_t)m * d);
+      du = u ? C->stage[2].p : nullptr;
+      dgr = grad ? C->stage[3].p : nullptr;
+      dt = tmap ? C->stage[4].p : nullptr;
+    }
+    potential_f64(C->st, m, d, C->n, side == 0 ? C->sX.p : C->sY.p, l, side == 0 ? C->sXf.p : C->sYf.p, dg,
+                  dP, C->sigma, C->lambda2, du, dgr, dt);
+    if (C->opt.host_pointers) {
+      dev_out(C, u, du, (size_t)m);
+      dev_out(C, grad, dgr, (size_t)m * d);
+      dev_out(C, tmap, dt, (size_t)m * d);
+    }
+    KOT_CUDA(cudaStreamSynchronize(C->st));
+  });
 }
 
 kot_status kot_dense_product(kot_ctx* C, int M, int N, int K, double alpha, const double* A,

@@ -172,6 +172,11 @@ void embed_f64(cudaStream_t st, int n, int d, int l, const double* S, const doub
 void pair_mean_f64(cudaStream_t st, int n, int d, const double* S, double inv2s2, double* out,
                    double* partial, int partial_cap);
 int pair_blocks(int n);                                            // partials the above needs
+// u(x_q), grad u(x_q), T(x_q) = x_q - grad u(x_q) at m query points Pq (m x d) from samples S
+// (n x d), filling points Sf (l x d) and dual weights gamma (any output may be null)
+void potential_f64(cudaStream_t st, int m, int d, int n, const double* S, int l, const double* Sf,
+                   const double* gamma, const double* Pq, double sigma, double lambda2, double* u,
+                   double* grad, double* tmap);
 void gram_f64(cudaStream_t st, int l, int d, const double* Xf, const double* Yf, double inv2s2,
               double lambda2, const double* w_mu, const double* w_nu, double* Q, double* K,
               double* c, double* z);

@@ -60,7 +60,8 @@ EXPORTS = ["kot_default_options", "kot_create", "kot_destroy", "kot_last_error",
            "kot_build_features", "kot_set_features", "kot_get_features", "kot_residual",
            "kot_newton_direction", "kot_ssn_solve", "kot_get_history", "kot_batch_solve",
            "kot_profile", "kot_profile_read", "kot_launch_count",
-           "kot_embedding_sqnorm_noalloc", "kot_dense_product", "kot_get_trace", "kot_eig_sym"]
+           "kot_embedding_sqnorm_noalloc", "kot_dense_product", "kot_get_trace", "kot_eig_sym",
+           "kot_eg_solve", "kot_potentials"]
 
 KERNEL_CLASSES = ["gemm_f64", "jacobi_f64", "jacobi_f32", "embed", "pair_sums", "gram",
                   "cholesky", "gemm_tc", "eig_refine", "gemm_oz", "oz_aux"]
@@ -101,6 +102,8 @@ def lib() -> C.CDLL:
         "kot_dense_product": (i, [vp, i, i, i, d, vp, i, i, vp, i, i, d, vp, i, i]),
         "kot_get_trace": (i, [vp, vp, i, C.POINTER(i)]),
         "kot_eig_sym": (i, [vp, i, vp, vp, vp, vp, C.POINTER(i)]),
+        "kot_eg_solve": (i, [vp, d, vp, vp, vp, vp, C.POINTER(Result)]),
+        "kot_potentials": (i, [vp, i, i, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -218,6 +221,20 @@ class Context:
         self._check(lib().kot_ssn_solve(self.h, tol, _ptr(gamma_out), _ptr(X_out), _ptr(gamma0),
                                         _ptr(X0), C.byref(r)), ok)
         return r
+
+    def eg_solve(self, tol, gamma_out, X_out=None, gamma0=None, X0=None,
+                 allow_no_convergence=False) -> Result:
+        """Pure extragradient (App. F) through kot_eg_solve."""
+        r = Result()
+        ok = (OK, ERR_NO_CONVERGENCE) if allow_no_convergence else (OK,)
+        self._check(lib().kot_eg_solve(self.h, tol, _ptr(gamma_out), _ptr(X_out), _ptr(gamma0),
+                                       _ptr(X0), C.byref(r)), ok)
+        return r
+
+    def potentials(self, side, m, points, gamma, u=None, grad=None, tmap=None):
+        """u (side 0) or v (side 1), its gradient and the map x - grad at m points."""
+        return self._check(lib().kot_potentials(self.h, side, m, _ptr(points), _ptr(gamma), _ptr(u),
+                                                _ptr(grad), _ptr(tmap)))
 
     def dense_product(self, M, N, K, alpha, A, lda, transA, B, ldb, transB, beta, Cm, ldc,
                       pieces=3):

@@ -247,6 +247,78 @@ def test_batch_matches_single_solves():
         assert ko.residual(F, N(g), np.zeros((p.l, p.l))).r1.shape == (p.l,)
 
 
+@pytest.mark.parametrize("precision,eta", [(0, 0.0), (0, 2e-3), (1, 0.0)])
+def test_pure_eg_matches_oracle(precision, eta):
+    # the pure extragradient method of App. F: a nonexpansive iteration (no 1/mu amplification),
+    # so the GPU and oracle sequences agree to rounding over many steps
+    p = WORKLOADS["paper_d2_l50"]()
+    F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
+    steps = 40
+    ref_eta = eta if eta > 0 else 1.0 / ko.eg_lipschitz(F)
+    ref_hist = [ko.residual(F, np.zeros(F.l), np.zeros((F.l, F.l))).norm]
+    g_ref, X_ref = np.zeros(F.l), np.zeros((F.l, F.l))
+    for _ in range(steps):
+        g_ref, X_ref = ko.eg_step(F, g_ref, X_ref, ref_eta)
+        ref_hist.append(ko.residual(F, g_ref, X_ref).norm)
+    ctx = kot.Context(device=0, precision=precision, max_iter=steps, eg_step=eta, record_history=1)
+    ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
+    g, X = Z(p.l), Z(p.l, p.l)
+    res = ctx.eg_solve(1e-12, g, X, allow_no_convergence=True)
+    assert res.status == kot.ERR_NO_CONVERGENCE and res.iters == steps and res.eg_taken == steps
+    rtol = 1e-9 if precision == 0 else 1e-7
+    np.testing.assert_allclose(ctx.history(), ref_hist, rtol=rtol)
+    np.testing.assert_allclose(N(g), g_ref, rtol=rtol, atol=rtol * np.abs(g_ref).max())
+    np.testing.assert_allclose(N(X), X_ref, atol=rtol * max(1.0, np.abs(X_ref).max()))
+    assert res.residual == pytest.approx(ko.residual(F, N(g), N(X)).norm, rel=1e-8)
+    assert ref_hist[-1] < ref_hist[1]
+
+
+@pytest.mark.parametrize("name,side", [("paper_d5_l97", 0), ("paper_d5_l97", 1), ("wide_d300", 0)])
+def test_potentials_match_oracle(name, side):
+    p = WORKLOADS[name]() if name in WORKLOADS else wl.paper_regime(seed=9, d=300, n=40, l=20, sigma2=30.0)
+    F, ctx = _features(p)
+    d = p.X.shape[1]
+    rng = np.random.default_rng(8)
+    gamma = 0.1 * rng.standard_normal(p.l)
+    m = 77                                   # ragged against the 256-source tiles
+    P = rng.uniform(0.0, 1.0, (m, d))
+    u, grad, tm = Z(m), Z(m, d), Z(m, d)
+    ctx.potentials(side, m, T(P), T(gamma), u, grad, tm)
+    S, Sf = (p.X, p.Xf) if side == 0 else (p.Y, p.Yf)
+    ru, rg, rt = ko.potential(S, Sf, gamma, p.sigma, p.lambda2, P)
+    np.testing.assert_allclose(N(u), ru, rtol=1e-12, atol=1e-13 * np.abs(ru).max())
+    np.testing.assert_allclose(N(grad), rg, rtol=1e-11, atol=1e-12 * np.abs(rg).max())
+    np.testing.assert_allclose(N(tm), rt, rtol=1e-12, atol=1e-12 * max(1.0, np.abs(rg).max()))
+    # the outputs are independent: u alone gives the same values
+    u2 = Z(m)
+    ctx.potentials(side, m, T(P), T(gamma), u2)
+    np.testing.assert_array_equal(N(u2), N(u))
+
+
+def test_potentials_reproduce_the_solved_estimator():
+    # after a GPU solve, <u, w_mu> + <v, w_nu> (potentials averaged over the samples) = OT-hat
+    p = WORKLOADS["paper_d2_l50"]()
+    F, ctx = _features(p)
+    g = Z(p.l)
+    res = ctx.ssn_solve(p.tol, g)
+    n = p.X.shape[0]
+    u, v = Z(n), Z(n)
+    ctx.potentials(0, n, T(p.X), g, u)
+    ctx.potentials(1, n, T(p.Y), g, v)
+    assert float(u.mean() + v.mean()) == pytest.approx(res.ot_hat, rel=1e-11)
+    # the map output alone equals x - grad u from a separate call (to the rounding of one
+    # fused multiply-add)
+    tm, gr = Z(n, 2), Z(n, 2)
+    ctx.potentials(0, n, T(p.X), g, None, None, tm)
+    ctx.potentials(0, n, T(p.X), g, None, gr, None)
+    np.testing.assert_allclose(N(tm), p.X - N(gr), rtol=0, atol=4e-16 * max(1.0, np.abs(N(tm)).max()))
+    c2 = kot.Context(device=0)
+    c2.set_features(T(F.Q), T(F.z), F.q2, T(F.R), F.lambda1, F.lambda2)
+    with pytest.raises(kot.KotError) as e:
+        c2.potentials(0, n, T(p.X), g, u)
+    assert e.value.status == kot.ERR_STATE
+
+
 def test_error_paths():
     ctx = kot.Context(device=0)
     g = Z(4)

@@ -327,6 +327,63 @@ def test_eg_is_monotone_descent_of_residual_on_average():
     assert r.residual < 0.5 * r0
 
 
+def test_eg_step_l1_is_scalar_projected_extragradient():
+    # l = 1 (R = [r], Q = [q]): the min-max operator is F(g, x) = ((q g - z)/(2 l2) - r^2 x,
+    # r^2 g + l1) on R x [0, inf), so one Korpelevich step is scalar projected gradient twice
+    q, r, z, l1, l2, eta = 1.7, 0.8, 0.3, 0.05, 0.1, 0.07
+    F = _features_direct(np.array([[q]]), np.array([z]), np.array([[r]]), l1, l2)
+    g0, x0 = -0.4, 0.9
+    Fg = lambda g, x: (q * g - z) / (2 * l2) - r * r * x
+    Fx = lambda g, x: r * r * g + l1
+    gh, xh = g0 - eta * Fg(g0, x0), max(0.0, x0 - eta * Fx(g0, x0))
+    g1, x1 = g0 - eta * Fg(gh, xh), max(0.0, x0 - eta * Fx(gh, xh))
+    gn, Xn = ko.eg_step(F, np.array([g0]), np.array([[x0]]), eta)
+    assert gn[0] == pytest.approx(g1, rel=1e-14)
+    assert Xn[0, 0] == pytest.approx(x1, rel=1e-14)
+
+
+def test_eg_step_fixes_a_solution():
+    # a solution w* of the variational inequality of Eq. (4.1) (R(w*) = 0) is a fixed point of
+    # the projected extragradient map for every step size
+    F = _small_features(l=6)
+    r = ko.ssn_solve(F, 1e-12, ko.Options(max_iter=500))
+    assert r.converged
+    for eta in (1e-3, 0.5 / ko.eg_lipschitz(F)):
+        g1, X1 = ko.eg_step(F, r.gamma, r.X, eta)
+        np.testing.assert_allclose(g1, r.gamma, atol=1e-9)
+        np.testing.assert_allclose(X1, r.X, atol=1e-9)
+
+
+def test_potentials_reproduce_the_estimator():
+    # <u, w_mu>_H = (1/n) sum_j u(x_j) (reproducing property), so averaging the potentials over
+    # the samples must give OT-hat = q^2/(2 l2) - sum_i gamma_i (w_mu(xf_i) + w_nu(yf_i))/(2 l2)
+    # as the paper prints it (Sec. 3), for any gamma
+    p = wl.paper_regime(seed=4, d=3, n=40, l=12)
+    F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
+    gamma = np.random.default_rng(3).standard_normal(F.l)
+    u, _, _ = ko.potential(p.X, p.Xf, gamma, p.sigma, p.lambda2, p.X)
+    v, _, _ = ko.potential(p.Y, p.Yf, gamma, p.sigma, p.lambda2, p.Y)
+    assert u.mean() + v.mean() == pytest.approx(ko.ot_estimate(F, gamma), rel=1e-12)
+
+
+def test_potential_gradient_and_map():
+    p = wl.paper_regime(seed=5, d=4, n=30, l=10)
+    gamma = np.random.default_rng(1).standard_normal(p.l)
+    P = np.random.default_rng(2).uniform(0.0, 1.0, (7, 4))
+    u, grad, T = ko.potential(p.X, p.Xf, gamma, p.sigma, p.lambda2, P)
+    h = 1e-6
+    for k in range(4):
+        e = np.zeros(4); e[k] = h
+        up, _, _ = ko.potential(p.X, p.Xf, gamma, p.sigma, p.lambda2, P + e)
+        um, _, _ = ko.potential(p.X, p.Xf, gamma, p.sigma, p.lambda2, P - e)
+        np.testing.assert_allclose(grad[:, k], (up - um) / (2 * h), rtol=1e-6, atol=1e-6 * np.abs(grad).max())
+    np.testing.assert_allclose(T, P - grad, rtol=0, atol=0)
+    # gamma = 0: u is the kernel mean embedding of mu-hat over 2 lambda2
+    u0, _, _ = ko.potential(p.X, p.Xf, np.zeros(p.l), p.sigma, p.lambda2, P)
+    emb = np.exp(-scipy.spatial.distance.cdist(P, p.X, "sqeuclidean") / (2 * p.sigma ** 2)).mean(axis=1)
+    np.testing.assert_allclose(u0, emb / (2 * p.lambda2), rtol=1e-13)
+
+
 # ---------------------------------------------------------------- planted mistakes
 def test_planted_mistakes_are_caught(monkeypatch):
     """Each mutation reproduces a plausible slip; the pin named beside it must reject it."""
