@@ -42,6 +42,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12     # SMs x FP64 FMA/clk x 2 flop
 # dominant O(l^3) product of each form (events around every other class's launches would only
 # perturb the latency-bound step; the per-class breakdown comes from one extra untimed step)
 ROOF_CLASS = {"mixed": "gemm_oz", "fp64": "gemm_f64"}
+PROFILE_EVERY = 8   # events around one launch in 8 of that class (less perturbation of the step)
 
 
 def make_problem(name: str, rank: int, step: int = 0):
@@ -207,6 +208,7 @@ def main():
         all_mask = (1 << len(kot.KERNEL_CLASSES)) - 1
         mask = {"roofline": 1 << kot.KERNEL_CLASSES.index(ROOF_CLASS[pname]), "all": all_mask,
                 "none": 0}[args.profile]
+        ctx.profile_every(PROFILE_EVERY if args.profile == "roofline" else 1)
         ctx.profile(mask)
         launches0 = kot.launch_count()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -231,6 +233,7 @@ def main():
         ms = sum(a.elapsed_time(b) for a, b in ev)
         stats = {name: ctx.profile_read(i) for i, name in enumerate(kot.KERNEL_CLASSES)}
         # per-class breakdown: one more step (untimed) with every class under events
+        ctx.profile_every(1)
         ctx.profile(all_mask)
         step(dprobs[0])
         torch.cuda.synchronize()
@@ -387,8 +390,10 @@ def report(args, probs, world, ms_max, ms_local, stats, launches, iters, conv, c
             achieved = (s.flops / s.launches) / (per_launch_ms * 1e-3) / 1e12
             roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
                         "unit": unit, "frac": achieved / peak, "traffic": None,
-                        "launches": s.launches, "avg_launch_us": per_launch_ms * 1e3,
-                        "share_of_step": s.ms / ms_local, "peak_source": peak_src}
+                        "launches_timed": s.launches, "timed_one_in": PROFILE_EVERY if args.profile == "roofline" else 1,
+                        "avg_launch_us": per_launch_ms * 1e3,
+                        "share_of_step": s.ms * (PROFILE_EVERY if args.profile == "roofline" else 1) / ms_local,
+                        "peak_source": peak_src}
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,

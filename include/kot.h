@@ -247,6 +247,9 @@ typedef struct {
 } kot_kernel_stats;
 
 kot_status kot_profile(kot_ctx* ctx, int mask);
+/* Time only one launch in `every` (>= 1, default 1) of each enabled class, so that the events
+ * perturb a latency-bound run less; the statistics then cover the sampled launches (clears them). */
+kot_status kot_profile_every(kot_ctx* ctx, int every);
 /* Total number of kernels this library has launched in the process so far (all contexts). */
 kot_status kot_launch_count(long long* out);
 kot_status kot_profile_read(kot_ctx* ctx, int cls, kot_kernel_stats* out);

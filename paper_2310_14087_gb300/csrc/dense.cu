@@ -62,7 +62,7 @@ void Profiler::collect() {
 
 void Profiler::reset() {
   collect();
-  for (int i = 0; i < KC_COUNT; ++i) launches[i] = 0, ms[i] = flops[i] = bytes[i] = 0.0;
+  for (int i = 0; i < KC_COUNT; ++i) launches[i] = seen[i] = 0, ms[i] = flops[i] = bytes[i] = 0.0;
 }
 
 void Profiler::release() {

@@ -1105,6 +1105,14 @@ kot_status kot_profile(kot_ctx* C, int mask) {
   });
 }
 
+kot_status kot_profile_every(kot_ctx* C, int every) {
+  if (!C || every < 1) return KOT_ERR_INVALID;
+  return run(C, [&] {
+    C->prof.reset();
+    C->prof.every = every;
+  });
+}
+
 kot_status kot_profile_read(kot_ctx* C, int cls, kot_kernel_stats* out) {
   if (!C || !out || cls < 0 || cls >= KC_COUNT) return KOT_ERR_INVALID;
   return run(C, [&] {

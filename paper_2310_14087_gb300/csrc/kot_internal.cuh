@@ -57,12 +57,16 @@ enum KClass : int {
 // flop and byte counts; collect() waits for the events and accumulates per class.
 struct Profiler {
   int mask = 0;
+  int every = 1;                       // time one launch in `every` of each enabled class
+  long long seen[KC_COUNT] = {};       // launches of each enabled class since the last reset
   struct Pending { int cls; cudaEvent_t a, b; double flops, bytes; };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
   long launches[KC_COUNT] = {};
   double ms[KC_COUNT] = {}, flops[KC_COUNT] = {}, bytes[KC_COUNT] = {};
   bool on(int cls) const { return (mask >> cls) & 1; }
+  // enabled, and this launch is one of the sampled ones
+  bool take(int cls) { return on(cls) && (seen[cls]++ % every) == 0; }
   cudaEvent_t get_event();
   void begin(cudaStream_t st, int cls, cudaEvent_t* a);
   void end(cudaStream_t st, int cls, cudaEvent_t a, double fl, double by);
@@ -81,7 +85,7 @@ struct ProfScope {
   double fl, by;
   cudaEvent_t a = nullptr;
   ProfScope(cudaStream_t s, int c, double f, double b) : p(current_profiler()), st(s), cls(c), fl(f), by(b) {
-    if (p && p->on(cls)) p->begin(st, cls, &a);
+    if (p && p->take(cls)) p->begin(st, cls, &a);
     else p = nullptr;
   }
   ~ProfScope() {
