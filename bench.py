@@ -43,6 +43,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12     # SMs x FP64 FMA/clk x 2 flop
 # perturb the latency-bound step; the per-class breakdown comes from one extra untimed step)
 ROOF_CLASS = {"mixed": "gemm_oz", "fp64": "gemm_f64"}
 PROFILE_EVERY = 8   # events around one launch in 8 of that class (less perturbation of the step)
+# DRAM bytes (read + write) of one k_oz_gemm launch of this workload's shape (300 x 300 x 300,
+# six slices) from an ncu capture (profiles/oz_gemm_emulated_fp64_l300_l1024.md); the
+# algorithmic bytes of that launch (the sliced operands) are 2 x 300 x 6 x 320 x 2 = 2.30 MB
+ROOF_TRAFFIC = {("gemm_oz", "paper_d5_n1000_l300"): 2340096.0}
 
 
 def make_problem(name: str, rank: int, step: int = 0):
@@ -161,9 +165,12 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true", help="do not time the host-buffer path")
     ap.add_argument("--profile", default="roofline", choices=["roofline", "all", "none"],
                     help="kernel classes timed with CUDA events inside the timed region")
-    ap.add_argument("--method", default="ssn", choices=["ssn", "eg"],
+    ap.add_argument("--method", default="ssn", choices=["ssn", "eg", "batch"],
                     help="ssn: Algorithm 2 (the headline); eg: the pure extragradient method of "
-                         "App. F, a fixed number of steps per problem")
+                         "App. F, a fixed number of steps per problem; batch: kot_batch_solve "
+                         "over an uneven batch (d 2..20, n 200..2000, l 32..512)")
+    ap.add_argument("--batch", type=int, default=32, help="problems per batch (--method batch)")
+    ap.add_argument("--workers", type=int, default=8, help="concurrent solves (--method batch)")
     ap.add_argument("--eg-steps", type=int, default=200, help="EG steps per problem (--method eg)")
     args = ap.parse_args()
 
@@ -183,6 +190,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device(dev))
     if args.method == "eg":
         return eg_bench(args, world, rank, local_rank, dev)
+    if args.method == "batch":
+        return batch_bench(args, world, rank, local_rank, dev)
     p = make_problem(args.workload, rank, 0)
     probs = [make_problem(args.workload, rank, k) for k in range(args.steps)]
     dprobs = [kot.DeviceProblem.from_problem(q, dev) for q in probs]
@@ -326,6 +335,60 @@ def eg_bench(args, world, rank, local_rank, dev):
         dist.destroy_process_group()
 
 
+def batch_bench(args, world, rank, local_rank, dev):
+    """Uneven batch through kot_batch_solve (largest problems first, --workers concurrent
+    solves with their own streams): each step solves one seeded batch to 1e-6.  Timed on the
+    host between device synchronisations (the workers' streams belong to the library)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2310_14087_gb300 import kot
+    prec = kot.MIXED if args.precision == "mixed" else kot.FP64
+    ctx = kot.Context(device=local_rank, precision=prec, batch_workers=args.workers)
+
+    def make(k):
+        probs = workloads.paper_regime_batch(count=args.batch, base_seed=50_000 + 10_000 * rank + 1000 * k)
+        return probs, [kot.DeviceProblem.from_problem(p, dev) for p in probs]
+
+    warm = [make(-1 - k) for k in range(args.warmup)]
+    steps = [make(k) for k in range(args.steps)]
+
+    def solve(item):
+        probs, dps = item
+        gs = [torch.zeros(p.l, dtype=torch.float64, device=dev) for p in probs]
+        return ctx.batch_solve(dps, gs)
+
+    for w in warm:
+        solve(w)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    results = [solve(st) for st in steps]
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    conv = sum(int(r.status == kot.OK) for res in results for r in res)
+    iters = [r.iters for res in results for r in res]
+    t = torch.tensor([secs], dtype=torch.float64, device=dev)
+    c = torch.tensor([float(conv)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "SSN solves/s to ||R||<=1e-6 over uneven batches (converged solves / wall s)",
+            "method": "batch", "value": float(c.item()) / float(t.item()), "unit": "solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(t.item()) / args.steps, "higher_is_better": True,
+            "scaling": "weak", "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "paper_regime_batch", "batch": args.batch, "workers": args.workers,
+                       "precision": args.precision, "d": "2..20", "n": "200..2000", "l": "32..512",
+                       "converged": conv, "problems": args.batch * args.steps * world,
+                       "mean_iters": float(np.mean(iters)), "timing": "host wall between device syncs"}}),
+              flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def end_to_end(args, p, main_prec, world, dev, local_rank):
     """The same problems through the C ABI with HOST buffers: the library copies each step's
     inputs in and gamma out inside the timed region."""
@@ -388,8 +451,11 @@ def report(args, probs, world, ms_max, ms_local, stats, launches, iters, conv, c
         roofline = None
         if dom is not None:
             achieved = (s.flops / s.launches) / (per_launch_ms * 1e-3) / 1e12
+            traffic = ROOF_TRAFFIC.get((dom, args.workload))
             roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
-                        "unit": unit, "frac": achieved / peak, "traffic": None,
+                        "unit": unit, "frac": achieved / peak, "traffic": traffic,
+                        "traffic_note": None if traffic is None else
+                        "ncu dram__bytes_read+write of one 300x300x300 six-slice launch (bytes)",
                         "launches_timed": s.launches, "timed_one_in": PROFILE_EVERY if args.profile == "roofline" else 1,
                         "avg_launch_us": per_launch_ms * 1e3,
                         "share_of_step": s.ms * (PROFILE_EVERY if args.profile == "roofline" else 1) / ms_local,

@@ -660,7 +660,7 @@ void gemv_f64(cudaStream_t st, int n, double alpha, const double* A, const doubl
 }
 
 // Arrays up to kOneBlockN entries are reduced by one block in one launch.
-constexpr size_t kOneBlockN = 1u << 17;
+constexpr size_t kOneBlockN = 1u << 14;
 
 void dot_f64(cudaStream_t st, int n, const double* x, const double* y, double* out,
              double* partial) {

@@ -65,18 +65,24 @@ constexpr int OZ_MAX_SLICES = 8;
 constexpr int OZ_MAX_PAIRS = OZ_MAX_SLICES * (OZ_MAX_SLICES + 1) / 2;
 constexpr int OZ_MAX_SPLITS = 8;
 constexpr int kSplitRows = 16;        // thread rows of a cluster slicing block (32 x 16 threads)
-constexpr int kOzClusterK = 8 * 64;   // K up to which one (portable, <= 8 block) cluster spans a row
+constexpr int kOzClusterK = 8 * 256;  // K up to which one (portable, <= 8 CTA) cluster spans a row
 
 inline int cdiv(size_t a, int b) { return (int)((a + b - 1) / b); }
 
 static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
 
-// SM count of the current device, queried once per device
-int sm_count() {
-  static int cache[64] = {};
+// ordinal of the current device (0..63)
+int device_index() {
   int dev = 0;
   KOT_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) throw Error{KOT_ERR_CUDA, "device ordinal out of range"};
+  return dev;
+}
+
+// SM count of the current device, queried once per device
+int sm_count() {
+  static int cache[64] = {};
+  const int dev = device_index();
   if (cache[dev] == 0) {
     int n = 0;
     KOT_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
@@ -436,24 +442,27 @@ __global__ void k_oz_split(OzSplitArgs a) {
   }
 }
 
-// Slicing for K <= kOzClusterK in one launch: a cluster of ceil(K / 64) blocks spans the K range
-// of 32 logical rows.  Each block keeps its 32 x 64 values in shared memory, publishes its
-// per-row maximum exponents, reads its peers' through distributed shared memory, and slices its
-// own values (no second pass over the operand, no second launch).  All blocks of a cluster share
-// blockIdx.y and blockIdx.z, so a cluster is either wholly inside the operand or wholly outside.
+// Slicing for K <= kOzClusterK in one launch: a cluster of at most 8 CTAs spans the K range of
+// 32 logical rows, each CTA 64 KW columns.  Each CTA keeps its values in shared memory, publishes
+// its per-row maximum exponents, reads its peers' through distributed shared memory, and slices
+// its own values (no second pass over the operand, no second launch).  All CTAs of a cluster
+// share blockIdx.y and blockIdx.z, so a cluster is either wholly inside the operand or outside.
+template <int KW>
 __global__ void __launch_bounds__(32 * kSplitRows) k_oz_split_cluster(OzSplitArgs a) {
+  constexpr int COLS = 64 * KW;
   cg::cluster_group cluster = cg::this_cluster();
   const OzOperand& o = a.op[blockIdx.z];
-  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * COLS;
   if (r0 >= o.rows) return;
   const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x kSplitRows
   const int s = a.s, Kp = a.Kp;
-  __shared__ double tile[32][65];                 // [row][k - k0]
+  extern __shared__ double tile_raw[];            // [32][COLS + 1]
+  double (*tile)[COLS + 1] = reinterpret_cast<double (*)[COLS + 1]>(tile_raw);
   __shared__ int pmax[32], se[32];
   if (o.trans) {
     const int r = r0 + tx;
 #pragma unroll
-    for (int kk = ty; kk < 64; kk += kSplitRows) {
+    for (int kk = ty; kk < COLS; kk += kSplitRows) {
       const int k = k0 + kk;
       tile[tx][kk] = (k < o.K && r < o.rows) ? oz_load(o, r, k) : 0.0;
     }
@@ -462,7 +471,7 @@ __global__ void __launch_bounds__(32 * kSplitRows) k_oz_split_cluster(OzSplitArg
     for (int i = ty; i < 32; i += kSplitRows) {
       const int r = r0 + i;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < 2 * KW; ++h) {
         const int k = k0 + tx + 32 * h;
         tile[i][tx + 32 * h] = (k < o.K && r < o.rows) ? oz_load(o, r, k) : 0.0;
       }
@@ -471,7 +480,9 @@ __global__ void __launch_bounds__(32 * kSplitRows) k_oz_split_cluster(OzSplitArg
   __syncthreads();
 #pragma unroll
   for (int i = ty; i < 32; i += kSplitRows) {
-    int e = max(biased_exp(tile[i][tx]), biased_exp(tile[i][tx + 32]));
+    int e = 0;
+#pragma unroll
+    for (int h = 0; h < 2 * KW; ++h) e = max(e, biased_exp(tile[i][tx + 32 * h]));
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, off));
     if (tx == 0) pmax[i] = e;
@@ -492,7 +503,7 @@ __global__ void __launch_bounds__(32 * kSplitRows) k_oz_split_cluster(OzSplitArg
     const int r = r0 + i;
     if (r >= o.rows) continue;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < 2 * KW; ++h) {
       const int k = k0 + tx + 32 * h;
       if (k >= Kp) continue;
       int d[OZ_MAX_SLICES];
@@ -506,6 +517,31 @@ __global__ void __launch_bounds__(32 * kSplitRows) k_oz_split_cluster(OzSplitArg
         }
     }
   }
+}
+
+template <int KW>
+void launch_split_cluster(cudaStream_t st, const OzSplitArgs& sa, int Kp, int rb) {
+  const int ncta = (Kp + 64 * KW - 1) / (64 * KW);
+  const size_t smem = (size_t)32 * (64 * KW + 1) * sizeof(double);
+  static bool attr[64] = {};   // the attribute is per device
+  const int dev = device_index();
+  if (!attr[dev]) {
+    KOT_CUDA(cudaFuncSetAttribute(k_oz_split_cluster<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr[dev] = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ncta, rb, 2);
+  cfg.blockDim = dim3(32, kSplitRows);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attrs[1];
+  attrs[0].id = cudaLaunchAttributeClusterDimension;
+  attrs[0].val.clusterDim.x = (unsigned)ncta;
+  attrs[0].val.clusterDim.y = 1;
+  attrs[0].val.clusterDim.z = 1;
+  cfg.attrs = attrs;
+  cfg.numAttrs = 1;
+  KOT_CUDA(cudaLaunchKernelEx(&cfg, k_oz_split_cluster<KW>, sa));
 }
 
 // ------------------------------------------------------------------ finalize
@@ -616,19 +652,10 @@ void gemm_oz(cudaStream_t st, OzWork& w, int M, int N, int K, const TcOperand& A
     // bytes: FP64 operands read twice, BF16 slices written
     ProfScope ps(st, KC_OZ_AUX, 0.0, 16.0 * ((double)M + N) * K + 2.0 * s * ((double)M + N) * Kp);
     if (K <= kOzClusterK) {
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(nkb, rb, 2);
-      cfg.blockDim = dim3(32, kSplitRows);
-      cfg.dynamicSmemBytes = 0;
-      cfg.stream = st;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = (unsigned)nkb;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      KOT_CUDA(cudaLaunchKernelEx(&cfg, k_oz_split_cluster, sa));
+      // widest CTA that keeps the cluster at <= 8 CTAs
+      if (Kp <= 8 * 64) launch_split_cluster<1>(st, sa, Kp, rb);
+      else if (Kp <= 8 * 128) launch_split_cluster<2>(st, sa, Kp, rb);
+      else launch_split_cluster<4>(st, sa, Kp, rb);
       KOT_LAUNCHED(1);
     } else {
       k_oz_rowexp<<<dim3(nkb, rb, 2), bs, 0, st>>>(sa);
@@ -655,10 +682,11 @@ void gemm_oz(cudaStream_t st, OzWork& w, int M, int N, int K, const TcOperand& A
   CUtensorMap ta, tb;
   std::memcpy(&ta, w.map_a, sizeof(ta));
   std::memcpy(&tb, w.map_b, sizeof(tb));
-  static bool attr_set = false;
-  if (!attr_set) {
+  static bool attr_set[64] = {};   // the attribute is per device
+  const int adev = device_index();
+  if (!attr_set[adev]) {
     KOT_CUDA(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
-    attr_set = true;
+    attr_set[adev] = true;
   }
   {
     // tensor work: np BF16 products of 2 M N K flops each (the FP64 product they stand for is

@@ -248,10 +248,13 @@ void gemm_tc(cudaStream_t st, TcWork& w, int M, int N, int K, const TcOperand& A
   KOT_LAUNCHED(2);
   const CUtensorMap ta = make_bf16_map(w.a.p, M, Ktot, TC_BM);
   const CUtensorMap tb = make_bf16_map(w.b.p, N, Ktot, TC_BN);
-  static bool attr_set = false;
-  if (!attr_set) {
+  static bool attr_set[64] = {};   // the attribute is per device
+  int adev = 0;
+  KOT_CUDA(cudaGetDevice(&adev));
+  if (adev < 0 || adev >= 64) throw Error{KOT_ERR_CUDA, "device ordinal out of range"};
+  if (!attr_set[adev]) {
     KOT_CUDA(cudaFuncSetAttribute(k_tc_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-    attr_set = true;
+    attr_set[adev] = true;
   }
   ProfScope ps(st, KC_GEMM_TC, 2.0 * M * N * (double)K * nseg, 2.0 * ((double)M + N) * Ktot + 8.0 * M * N);
   k_tc_gemm_bf16<<<dim3(cdiv(N, TC_BN), cdiv(M, TC_BM)), TC_THREADS, TC_SMEM, st>>>(ta, tb, C, M, N, Ktot, ldc,
