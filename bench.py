@@ -36,6 +36,7 @@ WORKLOADS = {
     "paper_d5_n1000_l300": dict(d=5, n=1000, l=300),
     "paper_d2_n100_l50": dict(d=2, n=100, l=50),
     "paper_d10_n2000_l1024": dict(d=10, n=2000, l=1024),
+    "paper_d64_n4000_l2048": dict(d=64, n=4000, l=2048),
 }
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12     # SMs x FP64 FMA/clk x 2 flops x max clock
 # kernel class whose launches are timed live inside the timed region for the roofline: the
@@ -170,6 +171,8 @@ def main():
                          "App. F, a fixed number of steps per problem; batch: kot_batch_solve "
                          "over an uneven batch (d 2..20, n 200..2000, l 32..512)")
     ap.add_argument("--batch", type=int, default=32, help="problems per batch (--method batch)")
+    ap.add_argument("--max-iter", type=int, default=200,
+                    help="outer-iteration cap of Algorithm 2 (lower it to time iterations at large l)")
     ap.add_argument("--workers", type=int, default=8, help="concurrent solves (--method batch)")
     ap.add_argument("--eg-steps", type=int, default=200, help="EG steps per problem (--method eg)")
     args = ap.parse_args()
@@ -204,7 +207,8 @@ def main():
     def timed(prec):
         """W warm-up steps, then K timed steps (CUDA events on the library's stream, L2 flushed
         before each step outside the events); returns ms, per-class stats, launches, iters."""
-        ctx = kot.Context(device=local_rank, stream=stream.cuda_stream, precision=prec)
+        ctx = kot.Context(device=local_rank, stream=stream.cuda_stream, precision=prec,
+                          max_iter=args.max_iter)
         g = torch.zeros(p.l, dtype=torch.float64, device=dev)
 
         def step(dp):

@@ -75,6 +75,10 @@ typedef struct {
   int eig_refine;          /* eigen-decompositions with a warm basis (the previous one of the
                               same sequence): at most this many refinement steps from it
                               before falling back to Jacobi sweeps; 0 = always Jacobi (default 5) */
+  int schur_solver;        /* Krylov method for the Schur system of Algorithm 1 (Sec. 4.3 names
+                              both): 0 = conjugate gradients (default), 1 = symmetric QMR
+                              (Freund-Nachtigal, no preconditioner); both stop on Eq. (4.3)
+                              measured with the true residual and cap at cg_max_iter */
 } kot_options;
 
 typedef struct {

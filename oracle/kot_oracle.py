@@ -58,6 +58,7 @@ class Options:
     jitter_max: float = 1e-6
     use_eg: bool = True            # Algorithm 2 safeguard on/off
     record_history: bool = False
+    schur_solver: int = 0          # 0: CG, 1: symmetric QMR (Sec. 4.3 names both)
 
 
 # ----------------------------------------------------------------------------------------
@@ -296,7 +297,7 @@ def newton_direction(F: Features, res: Residual, mu: float, opt: Options,
     """Algorithm 1. Solves (J_k + mu_k I)[dw] = -r_k inexactly (Eq. (4.3)).
 
     a1 = -r1 - Phi(r2 + T[r2])/(mu+1), a2 = -r2;
-    (Q/(2 lambda2) + mu I + Phi T Phi*) at1 = a1 by CG from 0;
+    (Q/(2 lambda2) + mu I + Phi T Phi*) at1 = a1 by CG (or symmetric QMR) from 0;
     at2 = (a2 + T[a2])/(mu+1);  dgamma = at1,  dX = at2 - T[Phi*(at1)].
 
     The full-system residual of an inexact at1 equals the CG residual (the second block row
@@ -339,19 +340,55 @@ def newton_direction(F: Features, res: Residual, mu: float, opt: Options,
             margin[0] = min(margin[0], abs(enorm - thr) / thr)
         return enorm <= thr
 
-    while not stop(x, TPx, ee) and it < (opt.cg_max_iter if cg_tol_abs is None else 10 * x.size + 50):
-        Hp, TPp = schur_matvec(p)
-        pHp = float(p @ Hp)
-        if pHp <= 0.0:
-            break
-        a = ee / pHp
-        x = x + a * p
-        TPx = TPx + a * TPp
-        e = e - a * Hp
-        ee_new = float(e @ e)
-        p = e + (ee_new / ee) * p
-        ee = ee_new
-        it += 1
+    cap = opt.cg_max_iter if cg_tol_abs is None else 10 * x.size + 50
+    if opt.schur_solver == 0:
+        while not stop(x, TPx, ee) and it < cap:
+            Hp, TPp = schur_matvec(p)
+            pHp = float(p @ Hp)
+            if pHp <= 0.0:
+                break
+            a = ee / pHp
+            x = x + a * p
+            TPx = TPx + a * TPp
+            e = e - a * Hp
+            ee_new = float(e @ e)
+            p = e + (ee_new / ee) * p
+            ee = ee_new
+            it += 1
+    else:
+        # Symmetric QMR without preconditioning (Freund and Nachtigal): the Lanczos/CG residual
+        # rl drives the recurrences, the iterate x moves along the smoothed direction d, and the
+        # true residual e = a1 - H x and T[Phi*(x)] are updated through H d and T[Phi*(d)].
+        rl = e.copy()
+        q = rl.copy()
+        tau_q = math.sqrt(float(rl @ rl))
+        theta = 0.0
+        rho = float(rl @ rl)
+        d = np.zeros_like(x)
+        Hd = np.zeros_like(x)
+        TPd = np.zeros_like(TPx)
+        while not stop(x, TPx, ee) and it < cap:
+            t, TPq = schur_matvec(q)
+            sig = float(q @ t)
+            if sig <= 0.0 or tau_q == 0.0:
+                break
+            a = rho / sig
+            rl = rl - a * t
+            theta_old = theta
+            theta = math.sqrt(float(rl @ rl)) / tau_q
+            c2 = 1.0 / (1.0 + theta * theta)
+            tau_q = tau_q * theta * math.sqrt(c2)
+            d = (c2 * theta_old * theta_old) * d + (c2 * a) * q
+            Hd = (c2 * theta_old * theta_old) * Hd + (c2 * a) * t
+            TPd = (c2 * theta_old * theta_old) * TPd + (c2 * a) * TPq
+            x = x + d
+            TPx = TPx + TPd
+            e = e - Hd
+            ee = float(e @ e)
+            rho_old = rho
+            rho = float(rl @ rl)
+            q = rl + (rho / rho_old) * q
+            it += 1
     return Direction(dgamma=x, dX=at2 - TPx, cg_iters=it, cg_res=math.sqrt(ee),
                      stop_margin=margin[0])
 

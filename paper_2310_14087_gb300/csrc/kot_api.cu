@@ -17,6 +17,10 @@
 
 using namespace kot;
 
+// layouts the ctypes binding mirrors (LP64, natural alignment)
+static_assert(sizeof(kot_options) == 176, "kot_options layout");
+static_assert(sizeof(kot_result) == 96, "kot_result layout");
+
 namespace {
 
 struct EigSlot {
@@ -64,7 +68,7 @@ struct kot_ctx {
   ResState rw, rv, rt;
   EigSlot ew, ev, et, e1, e2;
   DevBuf<double> M1, M2, M3, M4, M5, M6, TU, TV, TW, TG;
-  DevBuf<double> v1, v2, v3, v4, v5, v6;
+  DevBuf<double> v1, v2, v3, v4, v5, v6, w1, w2, w3;
   DevBuf<double> partial, scal, bounds;
   DevBuf<int> iscal;
   double* hs = nullptr;                        // pinned host scalars
@@ -112,6 +116,7 @@ void set_defaults(kot_options* o) {
   o->mixed_switch = 1e-4;
   o->batch_workers = 0;
   o->eig_refine = 5;
+  o->schur_solver = 0;
 }
 
 bool pos_finite(double v) { return std::isfinite(v) && v > 0.0; }
@@ -126,7 +131,8 @@ void ensure(kot_ctx* C, int l) {
                             &C->rw.r2, &C->rv.r2, &C->rt.r2})
     b->alloc(L2);
   for (DevBuf<double>* b : {&C->z, &C->w_mu, &C->w_nu, &C->c, &C->g, &C->vg, &C->tg, &C->dg,
-                            &C->v1, &C->v2, &C->v3, &C->v4, &C->v5, &C->v6, &C->rw.r1,
+                            &C->v1, &C->v2, &C->v3, &C->v4, &C->v5, &C->v6, &C->w1, &C->w2,
+                            &C->w3, &C->rw.r1,
                             &C->rv.r1, &C->rt.r1})
     b->alloc(L);
   for (EigSlot* e : {&C->ew, &C->ev, &C->et, &C->e1, &C->e2}) {
@@ -318,6 +324,80 @@ void t_apply(kot_ctx* C, const EigSlot& e, double mu, const double* S, double* o
   sym_sum(C->st, l, C->TG.p, S, 1.0 / mu, comp ? 1 : 0, out);
 }
 
+// Symmetric QMR (Freund and Nachtigal, no preconditioner) on H x = a1 from the x in dgam, whose
+// residual a1 - H x is in ev and T[Phi*(x)] in TPx.  The Lanczos residual rl drives the
+// recurrences; x moves along the smoothed direction d, and the true residual and T[Phi*(x)]
+// follow through H d and T[Phi*(d)], so the stopping test of Eq. (4.3) (or cg_tol_abs) sees the
+// returned iterate's own residual.  Returns the iterations; met = whether the test held.
+int sqmr_loop(kot_ctx* C, const ResState& r, const EigSlot& e, double mu, double cg_tol_abs, int cap,
+              const double* at2, const double* a1, double* dgam, double* TPx, double* ev, bool& met) {
+  (void)a1;
+  const int l = C->l;
+  const size_t L2 = (size_t)l * l;
+  cudaStream_t st = C->st;
+  double* rl = C->w1.p;      // Lanczos residual
+  double* q = C->v4.p;       // direction of the recurrences
+  double* t = C->v6.p;       // H q
+  double* d = C->w2.p;       // iterate update
+  double* Hd = C->w3.p;      // H d
+  double* TPd = C->M2.p;     // T[Phi*(d)]  (M2 is free once the right-hand side is formed)
+  KOT_CUDA(cudaMemcpyAsync(rl, ev, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  KOT_CUDA(cudaMemcpyAsync(q, ev, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  fill(st, l, 0.0, d);
+  fill(st, l, 0.0, Hd);
+  fill(st, L2, 0.0, TPd);
+  sumsq_f64(st, l, rl, C->scal.p, C->partial.p);
+  fetch(C, 1);
+  double rho = C->hs[0], tau_q = std::sqrt(rho), theta = 0.0;
+  int it = 0;
+  while (true) {
+    two_norms(st, l, dgam, L2, at2, TPx, C->scal.p + 1, C->partial.p);
+    sumsq_f64(st, l, ev, C->scal.p, C->partial.p);
+    fetch(C, 3);
+    const double enorm = std::sqrt(C->hs[0]);
+    if (!std::isfinite(enorm)) fail(KOT_ERR_NONFINITE, "QMR residual is not finite");
+    bool stop;
+    if (cg_tol_abs > 0) stop = enorm <= cg_tol_abs;
+    else {
+      const double dw = std::sqrt(C->hs[1]) + std::sqrt(C->hs[2]);
+      stop = enorm <= C->opt.tau * std::min(1.0, C->opt.kappa * r.norm * dw);
+    }
+    met = stop;
+    if (stop || it >= cap) break;
+    // t = H q, M6 = T[Phi*(q)]
+    phi_star_nd(C, q, C->M5.p);
+    t_apply(C, e, mu, C->M5.p, C->M6.p);
+    phi_nd(C, C->M6.p, C->v5.p, C->M5.p);
+    hmatvec(st, l, 1.0 / (2.0 * C->lambda2), C->Q.p, q, mu, C->v5.p, t);
+    dot_f64(st, l, q, t, C->scal.p + 3, C->partial.p);
+    fetch(C, 4);
+    const double sig = C->hs[3];
+    if (!(sig > 0.0) || tau_q == 0.0) break;
+    const double a = rho / sig;
+    axpby(st, l, 1.0, rl, -a, t, rl);
+    sumsq_f64(st, l, rl, C->scal.p + 4, C->partial.p);
+    KOT_CUDA(cudaMemcpyAsync(C->hs + 4, C->scal.p + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+    KOT_CUDA(cudaStreamSynchronize(st));
+    const double rr = C->hs[4];
+    const double theta_old = theta;
+    theta = std::sqrt(rr) / tau_q;
+    const double c2 = 1.0 / (1.0 + theta * theta);
+    tau_q = tau_q * theta * std::sqrt(c2);
+    const double f = c2 * theta_old * theta_old, g = c2 * a;
+    axpby(st, l, f, d, g, q, d);
+    axpby(st, l, f, Hd, g, t, Hd);
+    axpby(st, L2, f, TPd, g, C->M6.p, TPd);
+    axpby(st, l, 1.0, dgam, 1.0, d, dgam);
+    axpby(st, L2, 1.0, TPx, 1.0, TPd, TPx);
+    axpby(st, l, 1.0, ev, -1.0, Hd, ev);
+    const double rho_old = rho;
+    rho = rr;
+    axpby(st, l, 1.0, rl, rho / rho_old, q, q);
+    ++it;
+  }
+  return it;
+}
+
 // Algorithm 1 at w (residual r, eigen-decomposition e).  Returns CG iterations.
 // Mixed form: CG runs with tensor-core products first.  Its recursive residual belongs to the
 // inexact operator, so the test of Eq. (4.3) is then re-taken in FP64: the right-hand side is
@@ -367,46 +447,51 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
       axpby(st, l, 1.0, a1, -1.0, Hp, ev);
     }
     KOT_CUDA(cudaMemcpyAsync(pv, ev, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    // CG with its step lengths kept on the device: ||e||^2 alternates between scal[5] and
-    // scal[6], p^T H p is scal[3], scal[7] flags a non-positive curvature; the host reads the
-    // norms of the stopping test (and the flag) once per iteration
-    double* sc = C->scal.p;
-    int cur = 0, it = 0;
-    fill(st, 1, 0.0, sc + 7);
-    sumsq_f64(st, l, ev, sc + 5, C->partial.p);
-    while (true) {
-      // stop test at the current iterate: ||e|| vs tau min(1, kappa ||r|| ||dw||)
-      two_norms(st, l, dgam, L2, at2, TPx, sc + 1, C->partial.p);
-      fetch(C, 8);
-      const double ee = C->hs[5 + cur];
-      const double enorm = std::sqrt(ee);
-      if (!std::isfinite(enorm)) {
-        C->force64 = false;
-        fail(KOT_ERR_NONFINITE, "CG residual is not finite");
+    int it = 0;
+    if (C->opt.schur_solver == 1) {
+      it = sqmr_loop(C, r, e, mu, cg_tol_abs, cap, at2, a1, dgam, TPx, ev, met);
+    } else {
+      // CG with its step lengths kept on the device: ||e||^2 alternates between scal[5] and
+      // scal[6], p^T H p is scal[3], scal[7] flags a non-positive curvature; the host reads the
+      // norms of the stopping test (and the flag) once per iteration
+      double* sc = C->scal.p;
+      int cur = 0;
+      fill(st, 1, 0.0, sc + 7);
+      sumsq_f64(st, l, ev, sc + 5, C->partial.p);
+      while (true) {
+        // stop test at the current iterate: ||e|| vs tau min(1, kappa ||r|| ||dw||)
+        two_norms(st, l, dgam, L2, at2, TPx, sc + 1, C->partial.p);
+        fetch(C, 8);
+        const double ee = C->hs[5 + cur];
+        const double enorm = std::sqrt(ee);
+        if (!std::isfinite(enorm)) {
+          C->force64 = false;
+          fail(KOT_ERR_NONFINITE, "CG residual is not finite");
+        }
+        bool stop;
+        if (cg_tol_abs > 0) stop = enorm <= cg_tol_abs;
+        else {
+          const double dw = std::sqrt(C->hs[1]) + std::sqrt(C->hs[2]);
+          stop = enorm <= C->opt.tau * std::min(1.0, C->opt.kappa * r.norm * dw);
+        }
+        met = stop;
+        if (C->hs[7] != 0.0) {   // the last step met p^T H p <= 0 and was not taken
+          --it;
+          break;
+        }
+        if (stop || it >= cap) break;
+        // Hp = Q p/(2 lambda2) + mu p + Phi(T[Phi*(p)])
+        phi_star_nd(C, pv, C->M5.p);
+        t_apply(C, e, mu, C->M5.p, C->M6.p);
+        phi_nd(C, C->M6.p, C->v5.p, C->M5.p);
+        hmatvec(st, l, 1.0 / (2.0 * C->lambda2), C->Q.p, pv, mu, C->v5.p, Hp);
+        // a = ||e||^2 / p^T H p: x += a p, e -= a H p, p = e + b p (one block, scalars on the
+        // device), then T[Phi*(x)] += a T[Phi*(p)]
+        cg_step(st, l, Hp, pv, dgam, ev, sc, cur);
+        axpy_ratio(st, L2, sc + 5 + cur, sc + 3, 1.0, C->M6.p, TPx, nullptr);
+        cur ^= 1;
+        ++it;
       }
-      bool stop;
-      if (cg_tol_abs > 0) stop = enorm <= cg_tol_abs;
-      else {
-        const double dw = std::sqrt(C->hs[1]) + std::sqrt(C->hs[2]);
-        stop = enorm <= C->opt.tau * std::min(1.0, C->opt.kappa * r.norm * dw);
-      }
-      met = stop;
-      if (C->hs[7] != 0.0) {   // the last step met p^T H p <= 0 and was not taken
-        --it;
-        break;
-      }
-      if (stop || it >= cap) break;
-      // Hp = Q p/(2 lambda2) + mu p + Phi(T[Phi*(p)])
-      phi_star_nd(C, pv, C->M5.p);
-      t_apply(C, e, mu, C->M5.p, C->M6.p);
-      phi_nd(C, C->M6.p, C->v5.p, C->M5.p);
-      hmatvec(st, l, 1.0 / (2.0 * C->lambda2), C->Q.p, pv, mu, C->v5.p, Hp);
-      // a = ||e||^2 / p^T H p: x += a p, e -= a H p, p = e + b p (one block, scalars on the
-      // device), then T[Phi*(x)] += a T[Phi*(p)]
-      cg_step(st, l, Hp, pv, dgam, ev, sc, cur);
-      axpy_ratio(st, L2, sc + 5 + cur, sc + 3, 1.0, C->M6.p, TPx, nullptr);
-      cur ^= 1;
-      ++it;
     }
     total += it;
     if (phase == 1) refined_steps = it;
@@ -560,6 +645,7 @@ kot_status kot_create(kot_ctx** out, const kot_options* opt) {
       !(o.alpha1 > 0) || !(o.alpha2 >= o.alpha1) || !(o.beta0 > 0) || !(o.beta1 > 0) ||
       !(o.beta2 > 0) || !(o.theta0 > 0) || !(o.theta_min > 0) || !(o.theta_max >= o.theta_min) ||
       !(o.jitter >= 0) || !(o.jitter_max >= o.jitter) || o.eig_ctas < 0 || !(o.mixed_switch >= 0) || o.batch_workers < 0 || o.eig_refine < 0 ||
+      (o.schur_solver != 0 && o.schur_solver != 1) ||
       (o.precision != KOT_FP64 && o.precision != KOT_MIXED))
     return KOT_ERR_INVALID;
   int ndev = 0;
@@ -595,7 +681,8 @@ kot_status kot_destroy(kot_ctx* C) {
   for (DevBuf<double>* b : {&C->Q, &C->K, &C->R, &C->z, &C->w_mu, &C->w_nu, &C->c, &C->g, &C->X,
                             &C->vg, &C->vX, &C->tg, &C->tX, &C->dg, &C->dX, &C->M1, &C->M2,
                             &C->M3, &C->M4, &C->M5, &C->M6, &C->TU, &C->TV, &C->TW, &C->TG,
-                            &C->v1, &C->v2, &C->v3, &C->v4, &C->v5, &C->v6, &C->partial,
+                            &C->v1, &C->v2, &C->v3, &C->v4, &C->v5, &C->v6, &C->w1, &C->w2,
+                            &C->w3, &C->partial,
                             &C->scal, &C->bounds, &C->rw.r1, &C->rw.r2, &C->rv.r1, &C->rv.r2,
                             &C->rt.r1, &C->rt.r2, &C->eZ, &C->eP, &C->esig, &C->sX, &C->sY,
                             &C->sXf, &C->sYf})

@@ -34,7 +34,7 @@ class Options(C.Structure):
                 ("theta_max", C.c_double), ("eg_step", C.c_double), ("jitter", C.c_double),
                 ("jitter_max", C.c_double), ("use_eg", C.c_int), ("record_history", C.c_int),
                 ("eig_ctas", C.c_int), ("mixed_switch", C.c_double),
-                ("batch_workers", C.c_int), ("eig_refine", C.c_int)]
+                ("batch_workers", C.c_int), ("eig_refine", C.c_int), ("schur_solver", C.c_int)]
 
 
 class Result(C.Structure):

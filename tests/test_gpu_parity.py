@@ -117,6 +117,43 @@ def test_newton_direction_matches_oracle(name, scale, mu):
     np.testing.assert_allclose(N(dg), ref.dgamma, atol=1e-8 * scale_g)
 
 
+@pytest.mark.parametrize("name,scale,mu", [("paper_d2_l50", 0.05, 0.3), ("paper_d5_l97", 2.0, 1.0)])
+def test_sqmr_newton_direction_matches_oracle(name, scale, mu):
+    # symmetric QMR for the Schur system (the alternative Sec. 4.3 names): run to a tight
+    # tolerance it gives the same direction as the oracle; inexact, the same iterate and count
+    p = WORKLOADS[name]()
+    F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
+    ctx = kot.Context(device=0, schur_solver=1)
+    ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
+    g, X = _point(F, 11, scale)
+    res = ko.residual(F, g, X)
+    l = F.l
+    dg, dX = Z(l), Z(l, l)
+    ctx.newton_direction(T(g), T(X), mu, dg, dX, cg_tol_abs=1e-11)
+    ref = ko.newton_direction(F, res, mu, ko.Options(), cg_tol_abs=1e-11)
+    sg = np.abs(ref.dgamma).max()
+    np.testing.assert_allclose(N(dg), ref.dgamma, atol=1e-7 * sg)
+    np.testing.assert_allclose(N(dX), ref.dX, atol=1e-7 * max(np.abs(ref.dX).max(), sg))
+    it = ctx.newton_direction(T(g), T(X), mu, dg, dX)
+    ref = ko.newton_direction(F, res, mu, ko.Options(schur_solver=1))
+    assert it == ref.cg_iters
+    np.testing.assert_allclose(N(dg), ref.dgamma, atol=1e-8 * sg)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_with_sqmr(precision):
+    p = WORKLOADS["paper_d2_l50"]()
+    F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
+    ctx = kot.Context(device=0, precision=precision, schur_solver=1)
+    ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
+    g, X = Z(p.l), Z(p.l, p.l)
+    res = ctx.ssn_solve(p.tol, g, X)
+    assert res.status == kot.OK
+    assert ko.residual(F, N(g), N(X)).norm <= p.tol * (1 + 1e-6)
+    fstar, _ = _optimum(F)
+    assert res.objective == pytest.approx(fstar, rel=1e-6)
+
+
 def _solve_both(p, tol, **kw):
     F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
     ref = ko.ssn_solve(F, tol, ko.Options(record_history=True, **kw))

@@ -217,6 +217,28 @@ def test_algorithm1_equals_dense_newton_system(mu):
     np.testing.assert_allclose(d.dX, dX, rtol=1e-8, atol=1e-10)
 
 
+@pytest.mark.parametrize("mu", [0.05, 1.0])
+def test_sqmr_direction_equals_dense_newton_system(mu):
+    # the symmetric QMR option (Sec. 4.3 names CG or symmetric QMR) solves the same Schur system:
+    # run to a tight tolerance it must give the direction of the dense (l + l^2) Newton solve, and
+    # the true residual it carries must equal a1 - H x recomputed
+    F = _small_features(l=5)
+    rng = np.random.default_rng(4)
+    g, X = _point(F, rng)
+    res = ko.residual(F, g, 0.05 * X)
+    dg, dX = ind.dense_newton(F.Q, F.R, F.lambda2, res.eig.P, res.eig.sig, mu, res.r1, res.r2)
+    d = ko.newton_direction(F, res, mu, ko.Options(schur_solver=1), cg_tol_abs=1e-13)
+    np.testing.assert_allclose(d.dgamma, dg, atol=1e-9 * max(1.0, np.abs(dg).max()))
+    np.testing.assert_allclose(d.dX, dX, atol=1e-9 * max(1.0, np.abs(dX).max()))
+    # inexact: the carried residual is the true residual of the returned iterate
+    d = ko.newton_direction(F, res, mu, ko.Options(schur_solver=1, cg_max_iter=3), cg_tol_abs=1e-30)
+    Psi = ko.psi_matrix(res.eig.sig, mu)
+    T = lambda S: ko.t_apply(res.eig, Psi, S)
+    a1 = -res.r1 - ko.phi(F.R, res.r2 + T(res.r2)) / (mu + 1.0)
+    H = F.Q @ d.dgamma / (2 * F.lambda2) + mu * d.dgamma + ko.phi(F.R, T(ko.phi_star(F.R, d.dgamma)))
+    assert d.cg_res == pytest.approx(np.linalg.norm(a1 - H), rel=1e-8)
+
+
 def test_inexact_cg_residual_is_full_system_residual():
     rng = np.random.default_rng(9)
     F = _small_features(l=6)
