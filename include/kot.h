@@ -42,8 +42,11 @@ typedef enum {
 
 typedef enum {
   KOT_FP64 = 0,       /* every step in FP64                                             */
-  KOT_MIXED = 1       /* FP64 features/residual/stop test; FP32 eigen-solve with FP64
-                         refinement; reduced-precision Jacobian products inside CG         */
+  KOT_MIXED = 1       /* every O(l^3) product on the tcgen05 tensor cores: FP64-accuracy
+                         products (residual, projection, EG, eigenbasis refinement, Newton
+                         right-hand side and check) emulated with six fixed-point BF16
+                         slices; the Jacobian products inside CG with three (about FP32
+                         accuracy); FP64 features, Jacobi rotations, vectors and stop test  */
 } kot_precision;
 
 /* Algorithm constants.  Defaults (kot_default_options): the values of Sec. 5 for alpha1,
@@ -67,10 +70,11 @@ typedef struct {
   int use_eg;              /* 1: Algorithm 2 with the EG safeguard; 0: plain SSN steps   */
   int record_history;      /* 1: keep ||R(w_k)|| per iteration (kot_get_history)         */
   int eig_ctas;            /* CTAs of the cooperative Jacobi eigensolver; 0 = one per SM  */
-  double mixed_switch;     /* mixed form: tensor-core CG for the Newton direction while
-                              ||R(w_k)|| > this (its result is always re-checked against
-                              Eq. (4.3) in FP64 and finished in FP64 if short), plain FP64
-                              CG below it (default 1e-4)                                   */
+  double mixed_switch;     /* mixed form: reduced-precision (three-slice) CG products for the
+                              Newton direction while ||R(w_k)|| > this (the result is always
+                              re-checked against Eq. (4.3) with FP64-accuracy products and
+                              finished with them if short), FP64-accuracy CG products below
+                              it (default 1e-4)                                            */
   int batch_workers;       /* kot_batch_solve: problems solved concurrently (0 = 4)        */
   int eig_refine;          /* eigen-decompositions with a warm basis (the previous one of the
                               same sequence): at most this many refinement steps from it
