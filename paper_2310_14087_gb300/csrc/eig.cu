@@ -480,10 +480,10 @@ int jacobi_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
 namespace {
 
 // Refinement thresholds on max |E_ij|: above kRefineGiveUp the warm basis is too far for the
-// quadratic regime (or a pair is degenerate) and Jacobi takes over; at or below kRefineDone the
-// step just taken leaves an error of order kRefineDone^2 (below FP64 rounding), so it is the last.
+// quadratic regime (or a pair is degenerate) and Jacobi takes over; at or below w.refine_done
+// (1e-8 unless the caller asks otherwise) the step just taken leaves an error of order
+// refine_done^2, so it is the last.
 constexpr double kRefineGiveUp = 0.05;
-constexpr double kRefineDone = 1e-8;
 
 // Refine the warm basis into P, sig (ascending).  Returns the steps taken, or 0 if the iteration
 // gave up (P and sig are then untouched).
@@ -548,7 +548,7 @@ int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
     if (!(me <= kRefineGiveUp) || !(mr <= kRefineGiveUp)) return 0;
     X = Xn;
     ldX = ldx;
-    if (me <= kRefineDone && mr <= kRefineDone) {
+    if (me <= w.refine_done && mr <= w.refine_done) {
       k_rank_stride<<<cdiv(l, 32), dim3(32, 8), 0, st>>>(l, w.lam.p, 1, w.rank.p);
       k_gather_vec<<<g2, b2, 0, st>>>(l, w.lam.p, X, ldX, w.rank.p, P, sig);
       KOT_CHECK_LAUNCH();

@@ -225,6 +225,10 @@ void grad_gamma(kot_ctx* C, const double* gamma, const double* X, double* out, d
 void eig_into(kot_ctx* C, const double* Z, EigSlot& e, const EigSlot* warm) {
   const int l = C->l;
   const double* wp = (warm && warm->valid) ? warm->P.p : nullptr;
+  // Mixed form: a refinement whose correction is <= 1e-6 leaves a basis accurate to ~1e-12,
+  // below the accuracy of its emulated products; the eigenvalues (Rayleigh quotients, which decide
+  // alpha and Omega) are accurate to second order.  The FP64 form refines to FP64 rounding.
+  C->jw.refine_done = C->opt.precision == KOT_MIXED ? 1e-6 : 1e-8;
   C->eig_sweeps += eig_sym_f64(C->st, l, Z, wp, e.P.p, e.sig.p, C->jw, kMaxSweeps, C->hs,
                                C->opt.eig_ctas, C->opt.eig_refine);
   C->eig_calls += 1;
@@ -897,6 +901,7 @@ kot_status kot_eig_sym(kot_ctx* C, int l, const double* Z, const double* warm, d
     C->esig.alloc((size_t)l);
     copy_mat(C->st, l, l, dZ, l, C->eZ.p, l);
     symmetrize(C->st, l, C->eZ.p);
+    C->jw.refine_done = 1e-8;   // the building block always refines to FP64 rounding
     eig_sym_f64(C->st, l, C->eZ.p, dW, C->eP.p, C->esig.p, C->jw, kMaxSweeps, C->hs,
                 C->opt.eig_ctas, C->opt.eig_refine);
     dev_out(C, P, C->eP.p, L2);

@@ -196,6 +196,9 @@ void rowsum_bounds(cudaStream_t st, int l, const double* Q, const double* Kt, do
 struct OzWork;
 struct JacobiWork {
   OzWork* oz = nullptr;     // non-null: the eigensolver's products are emulated FP64 (tensor cores)
+  // a refinement step whose correction is at most this is the last one (the basis it leaves is
+  // accurate to about refine_done^2); 1e-8 leaves FP64 rounding
+  double refine_done = 1e-8;
   DevBuf<double> A, V;      // A: two lp x lp buffers; V: lp x lp
   DevBuf<double> rot;       // two rounds x lp/2 pairs x (c, s)
   DevBuf<int> pairs;        // lp

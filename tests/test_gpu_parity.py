@@ -441,6 +441,65 @@ def test_mixed_residual_matches_oracle(name, scale):
     assert N(norms)[2] == pytest.approx(ref.norm, rel=1e-9)
 
 
+def test_mixed_solve_full_size_bench_workload():
+    # the timed workload (d = 5, n = 1000, l = 300, Sec. 5 regime) in the form and launch
+    # configuration bench.py times: the oracle confirms the stopping test at the returned iterate
+    # and the objective sits within the tolerance-sized neighbourhood of the oracle's
+    p = wl.paper_regime(seed=1, d=5, n=1000, l=300)
+    F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
+    ref = ko.ssn_solve(F, p.tol)
+    ctx = kot.Context(device=0, precision=kot.MIXED)
+    ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
+    g, X = Z(p.l), Z(p.l, p.l)
+    res = ctx.ssn_solve(p.tol, g, X)
+    assert res.status == kot.OK
+    check = ko.residual(F, N(g), N(X))
+    assert check.norm <= p.tol * (1 + 1e-5)
+    assert res.residual == pytest.approx(check.norm, rel=1e-4, abs=1e-12)
+    assert res.objective == pytest.approx(ko.objective(F, N(g)), rel=1e-12)
+    if ref.converged:
+        assert res.objective == pytest.approx(ref.objective, rel=1e-4)
+
+
+def test_mixed_residual_sample_at_l1024():
+    # BASELINE's large-l shape (d = 10, n = 2000, l = 1024, Sec. 5 regime): the emulated-FP64
+    # residual map against the oracle's at one point
+    p = wl.paper_regime(seed=3, d=10, n=2000, l=1024)
+    F, _ = _features(p)
+    g, X = _point(F, 5, 0.3)
+    ref = ko.residual(F, g, X)
+    ctx = kot.Context(device=0, precision=kot.MIXED)
+    ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
+    l = F.l
+    r1, sig, norms = Z(l), Z(l), Z(3)
+    ctx.residual(T(g), T(X), r1, None, None, sig, norms)
+    zn = np.abs(ref.eig.sig).max()
+    np.testing.assert_allclose(N(sig), ref.eig.sig, atol=1e-11 * zn)
+    np.testing.assert_allclose(N(r1), ref.r1, rtol=1e-9, atol=1e-9 * np.abs(ref.r1).max())
+    assert N(norms)[2] == pytest.approx(ref.norm, rel=1e-9)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_degenerate_sizes_both_forms(precision):
+    # l = 1 (a scalar problem; closed form gamma = max(b/(2a), -lambda1/R11^2)) and the separable
+    # case Q = qI, R = I (gamma_i = max(z_i/q, -lambda1)) in both forms
+    ctx = kot.Context(device=0, precision=precision, max_iter=400)
+    Q, R, lam1, lam2, z1 = np.array([[1.7]]), np.array([[0.8]]), 0.05, 0.1, -0.5
+    ctx.set_features(T(Q), T(np.array([z1])), 1.0, T(R), lam1, lam2)
+    g = Z(1)
+    res = ctx.ssn_solve(1e-10, g)
+    a, b = Q[0, 0] / (4 * lam2), z1 / (2 * lam2)
+    assert N(g)[0] == pytest.approx(max(b / (2 * a), -lam1 / R[0, 0] ** 2), abs=1e-9)
+    rng = np.random.default_rng(10)
+    l, q = 37, 2.0
+    z = rng.uniform(-0.5, 0.5, l)
+    ctx.set_features(T(q * np.eye(l)), T(z), 1.0, T(np.eye(l)), lam1, lam2)
+    g = Z(l)
+    res = ctx.ssn_solve(1e-10, g)
+    np.testing.assert_allclose(N(g), np.maximum(z / q, -lam1), atol=1e-9)
+    assert res.residual <= 1e-10
+
+
 @pytest.mark.parametrize("name", ["paper_d2_l50", "paper_d5_l97"])
 def test_mixed_solve_gates(name):
     p = WORKLOADS[name]()
