@@ -171,6 +171,8 @@ def main():
                          "App. F, a fixed number of steps per problem; batch: kot_batch_solve "
                          "over an uneven batch (d 2..20, n 200..2000, l 32..512)")
     ap.add_argument("--batch", type=int, default=32, help="problems per batch (--method batch)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the (untimed) autotuning of split counts and Jacobi CTAs for l")
     ap.add_argument("--max-iter", type=int, default=200,
                     help="outer-iteration cap of Algorithm 2 (lower it to time iterations at large l)")
     ap.add_argument("--workers", type=int, default=8, help="concurrent solves (--method batch)")
@@ -196,6 +198,11 @@ def main():
     if args.method == "batch":
         return batch_bench(args, world, rank, local_rank, dev)
     p = make_problem(args.workload, rank, 0)
+    tuned = None
+    if not args.no_autotune:
+        # untimed: pick the emulated product's split counts and the Jacobi CTA count for this l
+        tuned = dict(zip(("splits_3_slices", "splits_6_slices", "jacobi_ctas"),
+                         kot.Context(device=local_rank).autotune(p.l)))
     probs = [make_problem(args.workload, rank, k) for k in range(args.steps)]
     dprobs = [kot.DeviceProblem.from_problem(q, dev) for q in probs]
     warm = [kot.DeviceProblem.from_problem(make_problem(args.workload, rank, -1 - k), dev)
@@ -278,7 +285,7 @@ def main():
     if rank == 0:
         report(args, probs, world, ms_max, ms_local, stats, launches, iters, conv, clocks, peaks,
                None if args.skip_other else (other_prec, o_value, o_ms_max, o_iters, o_conv), e2e,
-               float(conv_all.item()))
+               float(conv_all.item()), tuned)
     if world > 1:
         dist.destroy_process_group()
 
@@ -431,7 +438,7 @@ def end_to_end(args, p, main_prec, world, dev, local_rank):
 
 
 def report(args, probs, world, ms_max, ms_local, stats, launches, iters, conv, clocks, peaks, other,
-           e2e, conv_all):
+           e2e, conv_all, tuned=None):
     from paper_2310_14087_gb300 import kot
     value = conv_all / (ms_max / 1e3)          # converged solves per second, all ranks
     if True:
@@ -473,6 +480,7 @@ def report(args, probs, world, ms_max, ms_local, stats, launches, iters, conv, c
                        "precision": args.precision, "iters_per_solve": iters,
                        "converged": sum(conv), "ms_per_iteration": ms_local / max(1, sum(iters)),
                        "problems": "one seeded problem per step (seed 100 (rank+1) + step)",
+                       "autotuned": tuned,
                        "l2": "flushed before every step (256 MB write, untimed)"},
             "other_precision": None if other is None else {
                 "precision": "fp64" if other[0] == kot.FP64 else "mixed", "value": other[1],

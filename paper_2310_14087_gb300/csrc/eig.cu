@@ -577,6 +577,25 @@ int eig_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, dou
   return w.last_sweeps;
 }
 
+namespace {
+int g_tuned_ctas[64][32] = {};
+int l_bucket(int l) {
+  int b = 0;
+  while ((1 << b) < l && b < 31) ++b;
+  return b;
+}
+}  // namespace
+
+int tuned_jacobi_ctas(int dev, int l) {
+  if (dev < 0 || dev >= 64) return 0;
+  return g_tuned_ctas[dev][l_bucket(l)];
+}
+
+void set_tuned_jacobi_ctas(int dev, int l, int ctas) {
+  if (dev < 0 || dev >= 64) return;
+  g_tuned_ctas[dev][l_bucket(l)] = std::max(0, ctas);
+}
+
 int jacobi_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, double* P,
                    double* sig, JacobiWork& w, int max_sweeps, double* host_scal, int ctas) {
   const int lp = std::max(2, l + (l & 1));   // even, >= 2; a zero pad row/column never rotates
@@ -586,7 +605,9 @@ int jacobi_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
   KOT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   KOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_coop<double>, kCoopThreads, 0));
   if (per_sm < 1) throw Error{KOT_ERR_CUDA, "eig: cooperative kernel does not fit on an SM"};
-  // one CTA per SM by default (fewer arrivals per barrier than several per SM)
+  // one CTA per SM by default (fewer arrivals per barrier than several per SM), or the
+  // autotuner's choice for this size bucket
+  if (ctas <= 0) ctas = tuned_jacobi_ctas(dev, l);
   const int grid = ctas > 0 ? std::min(ctas, nsm * per_sm) : nsm;
   w.A.alloc(2 * (size_t)lp * lp);
   w.V.alloc((size_t)lp * lp);

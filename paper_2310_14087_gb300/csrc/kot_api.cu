@@ -1142,6 +1142,109 @@ kot_status kot_potentials(kot_ctx* C, int side, int m, const double* points, con
   });
 }
 
+namespace {
+// Pseudo-random entries in [-1, 1) from an integer hash of the index (inputs for the autotuner)
+__global__ void k_fill_hash(size_t n, unsigned seed, double* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    unsigned x = (unsigned)i * 2654435761u ^ seed;
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    out[i] = (double)x * (2.0 / 4294967296.0) - 1.0;
+  }
+}
+}  // namespace
+
+kot_status kot_autotune(kot_ctx* C, int l, int* choice) {
+  if (!C) return KOT_ERR_INVALID;
+  if (l < 1 || l > 32768) {
+    C->err = "kot_autotune: invalid argument";
+    return KOT_ERR_INVALID;
+  }
+  return run(C, [&] {
+    KOT_CUDA(cudaSetDevice(C->opt.device));
+    cudaStream_t st = C->st;
+    const int dev = C->opt.device;
+    const size_t L2 = (size_t)l * l;
+    DevBuf<double> A, B, Cm, P, sig;
+    A.alloc(L2);
+    B.alloc(L2);
+    Cm.alloc(L2);
+    P.alloc(L2);
+    sig.alloc((size_t)l);
+    const int fb = (int)std::min<size_t>((L2 + 255) / 256, 1216);
+    k_fill_hash<<<fb, 256, 0, st>>>(L2, 12345u, A.p);
+    k_fill_hash<<<fb, 256, 0, st>>>(L2, 67890u, B.p);
+    KOT_LAUNCHED(2);
+    KOT_CUDA(cudaPeekAtLastError());
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    KOT_CUDA(cudaEventCreate(&e0));
+    KOT_CUDA(cudaEventCreate(&e1));
+    struct EventGuard {
+      cudaEvent_t a, b;
+      ~EventGuard() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+      }
+    } guard{e0, e1};
+    auto timed = [&](const std::function<void()>& f, int reps) -> float {
+      f();                                   // warm (buffers, descriptors, caches)
+      KOT_CUDA(cudaEventRecord(e0, st));
+      for (int r = 0; r < reps; ++r) f();
+      KOT_CUDA(cudaEventRecord(e1, st));
+      KOT_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      KOT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      return ms / reps;
+    };
+    int best_split[2] = {0, 0};
+    const int slices[2] = {3, 6};
+    for (int q = 0; q < 2; ++q) {
+      float best = 1e30f;
+      for (int S : {1, 2, 3, 4, 6, 8, 12, 16}) {
+        C->oz.splits_override = S;
+        const float t = timed([&] {
+          gemm_oz(st, C->oz, l, l, l, TcOperand{A.p, l, false, nullptr}, TcOperand{B.p, l, true, nullptr},
+                  slices[q], 1.0, 0.0, Cm.p, l, false);
+        }, 5);
+        if (t < best) {
+          best = t;
+          best_split[q] = S;
+        }
+      }
+      C->oz.splits_override = 0;
+      set_tuned_splits(dev, l, slices[q], best_split[q]);
+    }
+    if (gemm_oz_error(st, C->oz)) fail(KOT_ERR_TIMEOUT, "tensor-core FP64-emulation wait timed out");
+    // cooperative Jacobi: CTA count for a cold decomposition of a symmetric l x l matrix
+    axpby(st, L2, 1.0, A.p, 0.0, nullptr, Cm.p);
+    symmetrize(st, l, Cm.p);
+    int nsm = 152;
+    KOT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    int best_ctas = nsm;
+    float best = 1e30f;
+    for (int ctas : {nsm / 4, nsm / 2, nsm}) {
+      if (ctas < 1) continue;
+      const float t = timed([&] {
+        eig_sym_f64(st, l, Cm.p, nullptr, P.p, sig.p, C->jw, kMaxSweeps, C->hs, ctas, 0);
+      }, 1);
+      if (t < best) {
+        best = t;
+        best_ctas = ctas;
+      }
+    }
+    set_tuned_jacobi_ctas(dev, l, best_ctas);
+    if (choice) {
+      choice[0] = best_split[0];
+      choice[1] = best_split[1];
+      choice[2] = best_ctas;
+    }
+    for (DevBuf<double>* b : {&A, &B, &Cm, &P, &sig}) b->release();
+  });
+}
+
 kot_status kot_dense_product(kot_ctx* C, int M, int N, int K, double alpha, const double* A,
                              int lda, int transA, const double* B, int ldb, int transB,
                              double beta, double* Cm, int ldc, int pieces) {

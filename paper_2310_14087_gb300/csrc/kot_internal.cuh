@@ -265,6 +265,7 @@ struct OzWork {
   DevBuf<float2> w;              // per-split partial sums
   DevBuf<int> err;               // set by a CTA whose bounded wait gave up
   int slices = 6;
+  int splits_override = 0;       // > 0: use this split count (the autotuner's probes)
   // last TMA descriptors (CUtensorMap, 128 bytes) and the (buffer, rows, cols) they describe
   alignas(64) unsigned char map_a[128], map_b[128];
   const void* key_a = nullptr;
@@ -282,6 +283,13 @@ struct OzWork {
 void gemm_oz(cudaStream_t st, OzWork& w, int M, int N, int K, const TcOperand& A, const TcOperand& B,
              int slices, double alpha, double beta, double* C, int ldc, bool sym);
 int gemm_oz_error(cudaStream_t st, OzWork& w);
+// Autotuner table: split count of the emulated product per device, size bucket of max(M, N)
+// (ceil log2) and slice count (0 = not tuned, use the occupancy rule).
+int tuned_splits(int dev, int mn, int slices);
+void set_tuned_splits(int dev, int mn, int slices, int splits);
+// Autotuner table for the cooperative Jacobi eigensolver: CTAs per size bucket (0 = one per SM).
+int tuned_jacobi_ctas(int dev, int l);
+void set_tuned_jacobi_ctas(int dev, int l, int ctas);
 // gemm_f64's interface (C = alpha opA(A) diag(s) opB(B) + beta C, triangular/symmetric flags):
 // on the FP64 pipes when oz is null, else emulated on the tensor cores with oz->slices slices
 // (the triangular flags only cut work on the FP64 pipes; G_SYM is honoured by both).

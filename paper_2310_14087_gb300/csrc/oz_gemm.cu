@@ -63,7 +63,7 @@ constexpr int OZ_EXACT_LEVELS = 4;
 constexpr int OZ_EXACT_TILES = 8;                // 8 x 64 products of |.| <= 2^14: sum <= 2^23
 constexpr int OZ_MAX_SLICES = 8;
 constexpr int OZ_MAX_PAIRS = OZ_MAX_SLICES * (OZ_MAX_SLICES + 1) / 2;
-constexpr int OZ_MAX_SPLITS = 8;
+constexpr int OZ_MAX_SPLITS = 16;
 constexpr int kSplitRows = 16;        // thread rows of a cluster slicing block (32 x 16 threads)
 constexpr int kOzClusterK = 8 * 256;  // K up to which one (portable, <= 8 CTA) cluster spans a row
 
@@ -89,6 +89,16 @@ int sm_count() {
     cache[dev] = n;
   }
   return cache[dev];
+}
+
+// Split counts chosen by the autotuner, per device, size bucket (ceil log2 of max(M, N)) and
+// slice count; 0 = not tuned.
+int g_tuned_splits[64][32][OZ_MAX_SLICES + 1] = {};
+
+int size_bucket(int mn) {
+  int b = 0;
+  while ((1 << b) < mn && b < 31) ++b;
+  return b;
 }
 
 struct OzPlan {
@@ -612,7 +622,13 @@ void gemm_oz(cudaStream_t st, OzWork& w, int M, int N, int K, const TcOperand& A
     }
   P.npairs = np;
   const int tiles = cdiv(N, OZ_BN) * cdiv(M, OZ_BM);
-  const int splits = std::max(1, std::min({OZ_MAX_SPLITS, np * (Kp / OZ_BK), nsm / tiles}));
+  // split count: the autotuner's choice for this size bucket and slice count if there is one,
+  // else enough splits to give every SM a CTA; w.splits_override (the tuner's probe) wins
+  int want = std::max(1, nsm / tiles);
+  const int tuned = tuned_splits(device_index(), std::max(M, N), s);
+  if (tuned > 0) want = tuned;
+  if (w.splits_override > 0) want = w.splits_override;
+  const int splits = std::max(1, std::min({OZ_MAX_SPLITS, np * (Kp / OZ_BK), want}));
   const int T = np * P.nk;   // tile steps (pair, k tile) of one output tile
   for (int z = 0; z <= splits; ++z) P.sbeg[z] = (int)((long long)z * T / splits);
 
@@ -703,6 +719,16 @@ void gemm_oz(cudaStream_t st, OzWork& w, int M, int N, int K, const TcOperand& A
     k_oz_finalize<<<fgrid, 256, 0, st>>>(M, N, splits, w.w.p, w.fac.p, w.fac.p + M, beta, C, ldc, sym ? 1 : 0);
     KOT_LAUNCHED(1);
   }
+}
+
+int tuned_splits(int dev, int mn, int slices) {
+  if (dev < 0 || dev >= 64 || slices < 0 || slices > OZ_MAX_SLICES) return 0;
+  return g_tuned_splits[dev][size_bucket(mn)][slices];
+}
+
+void set_tuned_splits(int dev, int mn, int slices, int splits) {
+  if (dev < 0 || dev >= 64 || slices < 0 || slices > OZ_MAX_SLICES) return;
+  g_tuned_splits[dev][size_bucket(mn)][slices] = std::max(0, std::min(splits, OZ_MAX_SPLITS));
 }
 
 int gemm_oz_error(cudaStream_t st, OzWork& w) {

@@ -61,7 +61,7 @@ EXPORTS = ["kot_default_options", "kot_create", "kot_destroy", "kot_last_error",
            "kot_newton_direction", "kot_ssn_solve", "kot_get_history", "kot_batch_solve",
            "kot_profile", "kot_profile_read", "kot_launch_count",
            "kot_embedding_sqnorm_noalloc", "kot_dense_product", "kot_get_trace", "kot_eig_sym",
-           "kot_eg_solve", "kot_potentials", "kot_profile_every"]
+           "kot_eg_solve", "kot_potentials", "kot_profile_every", "kot_autotune"]
 
 KERNEL_CLASSES = ["gemm_f64", "jacobi_f64", "jacobi_f32", "embed", "pair_sums", "gram",
                   "cholesky", "gemm_tc", "eig_refine", "gemm_oz", "oz_aux"]
@@ -98,6 +98,7 @@ def lib() -> C.CDLL:
         "kot_batch_solve": (i, [vp, i, C.POINTER(Problem), C.POINTER(Result)]),
         "kot_profile": (i, [vp, i]),
         "kot_profile_every": (i, [vp, i]),
+        "kot_autotune": (i, [vp, i, vp]),
         "kot_profile_read": (i, [vp, i, C.POINTER(KernelStats)]),
         "kot_launch_count": (i, [C.POINTER(C.c_longlong)]),
         "kot_dense_product": (i, [vp, i, i, i, d, vp, i, i, vp, i, i, d, vp, i, i]),
@@ -252,6 +253,13 @@ class Context:
 
     def profile(self, mask: int):
         return self._check(lib().kot_profile(self.h, mask))
+
+    def autotune(self, l: int):
+        """Tune the emulated product's split counts and the Jacobi CTA count for size l; returns
+        (splits with 3 slices, splits with 6 slices, Jacobi CTAs)."""
+        out = (C.c_int * 3)()
+        self._check(lib().kot_autotune(self.h, l, out))
+        return out[0], out[1], out[2]
 
     def profile_every(self, every: int):
         return self._check(lib().kot_profile_every(self.h, every))

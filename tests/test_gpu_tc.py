@@ -160,3 +160,29 @@ def test_emulated_fp64_rejects_bad_slices():
         with pytest.raises(kot.KotError) as e:
             ctx.dense_product(4, 4, 4, 1.0, x, 4, 0, x, 4, 0, 0.0, x, 4, pieces=bad)
         assert e.value.status == kot.ERR_INVALID
+
+
+def test_autotune_records_valid_choices():
+    # the autotuner picks a split count per slice count and a Jacobi CTA count for the size
+    # bucket; products and decompositions afterwards still meet their accuracy bounds
+    ctx = kot.Context(device=0)
+    s3, s6, ctas = ctx.autotune(97)
+    assert s3 in (1, 2, 3, 4, 6, 8, 12, 16) and s6 in (1, 2, 3, 4, 6, 8, 12, 16)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert ctas in (sms // 4, sms // 2, sms)
+    rng = np.random.default_rng(1)
+    M = N = K = 97
+    A, B = rng.standard_normal((M, K)), rng.standard_normal((N, K))
+    Cm = torch.zeros((M, N), dtype=torch.float64, device=DEV)
+    ctx.dense_product(M, N, K, 1.0, torch.as_tensor(A, device=DEV), K, 0, torch.as_tensor(B, device=DEV),
+                      K, 0, 0.0, Cm, N, pieces=-6)
+    bound = (2.0 ** -42 + 2.0 ** -44) * K * np.outer(np.abs(A).max(1), np.abs(B).max(1))
+    assert np.all(np.abs(Cm.cpu().numpy() - A @ B.T) <= bound)
+    Zs = rng.standard_normal((M, M))
+    Zs = Zs + Zs.T
+    P, sig = torch.zeros((M, M), dtype=torch.float64, device=DEV), torch.zeros(M, dtype=torch.float64, device=DEV)
+    ctx.eig_sym(M, torch.as_tensor(Zs, device=DEV), None, P, sig)
+    np.testing.assert_allclose(sig.cpu().numpy(), np.linalg.eigvalsh(Zs), atol=1e-12 * np.abs(Zs).max() * M)
+    with pytest.raises(kot.KotError) as e:
+        ctx.autotune(0)
+    assert e.value.status == kot.ERR_INVALID
