@@ -270,7 +270,7 @@ struct OzWork {
   alignas(64) unsigned char map_a[128], map_b[128];
   const void* key_a = nullptr;
   const void* key_b = nullptr;
-  int rows_a = 0, cols_a = 0, rows_b = 0, cols_b = 0;
+  int rows_a = 0, cols_a = 0, rows_b = 0, cols_b = 0, box_b = 0;
   void release() {
     a.release();
     b.release();

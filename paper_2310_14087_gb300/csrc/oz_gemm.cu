@@ -53,12 +53,22 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 64, OZ_STAGES = 6, OZ_THREADS = 192;
+constexpr int OZ_BM = 128, OZ_BK = 64, OZ_STAGES = 6;
 constexpr int OZ_A_BYTES = OZ_BM * OZ_BK * 2;   // 16 KB
-constexpr int OZ_B_BYTES = OZ_BN * OZ_BK * 2;   // 8 KB
-constexpr int OZ_STAGE = OZ_A_BYTES + OZ_B_BYTES;
-constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + 1024 + 256;
-constexpr int OZ_TMEM_COLS = 2 * OZ_BN;          // two accumulator buffers
+
+// Tile configuration by output-tile width BN (64 or 128): BN / 16 epilogue warps, each owning 64
+// accumulator columns of one 32-lane quarter of tensor memory, then the TMA producer warp and
+// the MMA warp.
+template <int BN>
+struct OzCfg {
+  static constexpr int EPI = BN / 16;                       // epilogue warps
+  static constexpr int THREADS = 32 * (EPI + 2);
+  static constexpr int B_BYTES = BN * OZ_BK * 2;            // 8 or 16 KB
+  static constexpr int STAGE = OZ_A_BYTES + B_BYTES;
+  static constexpr int SMEM = OZ_STAGES * STAGE + 1024 + 256;
+  static constexpr int TMEM_COLS = 2 * BN;                  // two accumulator buffers
+  static_assert(EPI * 32 * 65 * 8 <= OZ_STAGES * STAGE, "epilogue staging fits in the ring");
+};
 constexpr int OZ_EXACT_LEVELS = 4;
 constexpr int OZ_EXACT_TILES = 8;                // 8 x 64 products of |.| <= 2^14: sum <= 2^23
 constexpr int OZ_MAX_SLICES = 8;
@@ -126,9 +136,12 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float g) {
   lo = __fadd_rn(lo, e);
 }
 
-__global__ void __launch_bounds__(OZ_THREADS, 1)
+template <int BN>
+__global__ void __launch_bounds__(OzCfg<BN>::THREADS, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
               const __grid_constant__ OzPlan P) {
+  using Cfg = OzCfg<BN>;
+  constexpr int EPI = Cfg::EPI, OZ_STAGE = Cfg::STAGE, OZ_BN = BN;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + OZ_STAGES * OZ_STAGE);
@@ -150,19 +163,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 4);
+      mbar_init(&acc_empty[b], EPI);
     }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(tmem_slot, OZ_TMEM_COLS);
+  if (warp == 0) tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
 
-  if (warp == 4) {
+  if (warp == EPI) {
     if (lane == 0) {
       // TMA producer: the tiles of this split's steps, in order (counters kept incrementally:
       // this thread is on the critical path)
@@ -187,7 +200,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         }
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == EPI + 1) {
     if (lane == 0) {
       // MMA issuer
       constexpr uint32_t idesc = idesc_bf16(OZ_BM, OZ_BN);
@@ -237,7 +250,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       if (!mbar_wait(done, 0)) ok = false;
     }
   } else {
-    // epilogue warps 0-3: warp w owns accumulator lanes (output rows) 32 w .. 32 w + 31
+    // epilogue warps: warp w owns accumulator lanes (output rows) 32 (w % 4) .. + 31 and the 64
+    // columns starting at 64 (w / 4)
+    const int quarter = warp & 3, ch = 64 * (warp >> 2);
     int G = 0;
     {
       int gt = 0, prev = -1, p = s0 / nk, kt = s0 - p * nk;
@@ -255,18 +270,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         }
       }
     }
-    float hi[OZ_BN], lo[OZ_BN];
+    float hi[64], lo[64];
 #pragma unroll
-    for (int j = 0; j < OZ_BN; ++j) hi[j] = lo[j] = 0.0f;
+    for (int j = 0; j < 64; ++j) hi[j] = lo[j] = 0.0f;
     for (int g = 0; g < G; ++g) {
       if (!mbar_wait(&acc_full[g & 1], ((uint32_t)g >> 1) & 1u)) {
         ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((g & 1) * OZ_BN);
+      const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((g & 1) * OZ_BN + ch);
 #pragma unroll
-      for (int h = 0; h < OZ_BN / 32; ++h) {
+      for (int h = 0; h < 2; ++h) {
         uint32_t r[32];
         tmem_ld_32cols(base + 32 * h, r);
 #pragma unroll
@@ -280,19 +295,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       // Every MMA has completed (the last group's commit covers them), so the operand ring is
       // free: each warp stages its 32 x 64 (hi, lo) block there and writes it back row by row,
       // 32 consecutive columns per store instruction.
-      float2* buf = (float2*)(smem + (size_t)warp * 32 * (OZ_BN + 1) * sizeof(float2));
+      float2* buf = (float2*)(smem + (size_t)warp * 32 * 65 * sizeof(float2));
 #pragma unroll
-      for (int j = 0; j < OZ_BN; ++j) buf[lane * (OZ_BN + 1) + j] = make_float2(hi[j], lo[j]);
+      for (int j = 0; j < 64; ++j) buf[lane * 65 + j] = make_float2(hi[j], lo[j]);
       __syncwarp();
-      const int rbase = m0 + warp * 32;
+      const int rbase = m0 + quarter * 32;
       for (int rr = 0; rr < 32; ++rr) {
         const int row = rbase + rr;
         if (row >= P.M) break;
         float2* wr = P.W + ((size_t)z * P.M + row) * P.N;
 #pragma unroll
-        for (int h = 0; h < OZ_BN / 32; ++h) {
-          const int col = n0 + 32 * h + lane;
-          if (col < P.N) wr[col] = buf[rr * (OZ_BN + 1) + 32 * h + lane];
+        for (int h = 0; h < 2; ++h) {
+          const int col = n0 + ch + 32 * h + lane;
+          if (col < P.N) wr[col] = buf[rr * 65 + 32 * h + lane];
         }
       }
     }
@@ -300,7 +315,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   if (!ok) atomicExch(P.err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, OZ_TMEM_COLS);
+  if (warp == 0) tmem_dealloc(tmem, Cfg::TMEM_COLS);
 }
 
 // ------------------------------------------------------------------ slicing
@@ -592,6 +607,21 @@ __global__ void k_oz_finalize(int M, int N, int splits, const float2* __restrict
 
 }  // namespace
 
+namespace {
+template <int BN>
+void launch_oz_gemm(cudaStream_t st, const CUtensorMap& ta, const CUtensorMap& tb, const OzPlan& P, int M, int N,
+                    int splits) {
+  using Cfg = OzCfg<BN>;
+  static bool attr_set[64] = {};   // the attribute is per device
+  const int dev = device_index();
+  if (!attr_set[dev]) {
+    KOT_CUDA(cudaFuncSetAttribute(k_oz_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
+    attr_set[dev] = true;
+  }
+  k_oz_gemm<BN><<<dim3(cdiv(N, BN), cdiv(M, OZ_BM), splits), Cfg::THREADS, Cfg::SMEM, st>>>(ta, tb, P);
+}
+}  // namespace
+
 void gemm_oz(cudaStream_t st, OzWork& w, int M, int N, int K, const TcOperand& A, const TcOperand& B,
              int slices, double alpha, double beta, double* C, int ldc, bool sym) {
   if (M <= 0 || N <= 0) return;
@@ -621,7 +651,9 @@ void gemm_oz(cudaStream_t st, OzWork& w, int M, int N, int K, const TcOperand& A
       ++np;
     }
   P.npairs = np;
-  const int tiles = cdiv(N, OZ_BN) * cdiv(M, OZ_BM);
+  // wide tiles for large products: twice the MMA work per 64-wide K step for 1.33x the bytes
+  const int BNsel = (M >= 512 && N >= 512) ? 128 : 64;
+  const int tiles = cdiv(N, BNsel) * cdiv(M, OZ_BM);
   // split count: the autotuner's choice for this size bucket and slice count if there is one,
   // else enough splits to give every SM a CTA; w.splits_override (the tuner's probe) wins
   int want = std::max(1, nsm / tiles);
@@ -688,28 +720,24 @@ void gemm_oz(cudaStream_t st, OzWork& w, int M, int N, int K, const TcOperand& A
     w.rows_a = M;
     w.cols_a = s * Kp;
   }
-  if (w.key_b != w.b.p || w.rows_b != N || w.cols_b != s * Kp) {
-    const CUtensorMap m = make_bf16_map(w.b.p, N, s * Kp, OZ_BN);
+  if (w.key_b != w.b.p || w.rows_b != N || w.cols_b != s * Kp || w.box_b != BNsel) {
+    const CUtensorMap m = make_bf16_map(w.b.p, N, s * Kp, BNsel);
     std::memcpy(w.map_b, &m, sizeof(m));
     w.key_b = w.b.p;
     w.rows_b = N;
     w.cols_b = s * Kp;
+    w.box_b = BNsel;
   }
   CUtensorMap ta, tb;
   std::memcpy(&ta, w.map_a, sizeof(ta));
   std::memcpy(&tb, w.map_b, sizeof(tb));
-  static bool attr_set[64] = {};   // the attribute is per device
-  const int adev = device_index();
-  if (!attr_set[adev]) {
-    KOT_CUDA(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
-    attr_set[adev] = true;
-  }
   {
     // tensor work: np BF16 products of 2 M N K flops each (the FP64 product they stand for is
     // 2 M N K); bytes: the BF16 slices in, the float2 partial sums out
     ProfScope ps(st, KC_GEMM_OZ, 2.0 * M * N * (double)K * np,
                  2.0 * s * ((double)M + N) * Kp + 8.0 * splits * (double)M * N);
-    k_oz_gemm<<<dim3(cdiv(N, OZ_BN), cdiv(M, OZ_BM), splits), OZ_THREADS, OZ_SMEM, st>>>(ta, tb, P);
+    if (BNsel == 128) launch_oz_gemm<128>(st, ta, tb, P, M, N, splits);
+    else launch_oz_gemm<64>(st, ta, tb, P, M, N, splits);
     KOT_LAUNCHED(1);
   }
   const size_t MN = (size_t)M * N;

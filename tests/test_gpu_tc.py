@@ -112,7 +112,9 @@ def test_fp64_product_is_deterministic():
 EMU_SHAPES = [(300, 300, 300, 0, 1, 6), (300, 300, 300, 1, 0, 6), (1, 7, 5, 0, 0, 6),
               (257, 130, 513, 1, 0, 6), (64, 300, 97, 1, 1, 7), (513, 511, 1025, 0, 0, 6),
               (16, 16, 1, 0, 1, 3), (1024, 1024, 1024, 0, 0, 6), (129, 257, 2100, 0, 1, 8),
-              (300, 22, 300, 1, 1, 4)]
+              (300, 22, 300, 1, 1, 4),
+              # 128 x 128 output tiles (M, N >= 512), ragged edges and both transposes
+              (600, 700, 900, 1, 0, 6), (1000, 513, 300, 0, 1, 3), (520, 1030, 64, 1, 1, 7)]
 
 
 @pytest.mark.parametrize("M,N,K,ta,tb,s", EMU_SHAPES)
