@@ -45,7 +45,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12     # SMs x FP64 FMA/clk x 2 flop
 ROOF_CLASS = {"mixed": "gemm_oz", "fp64": "gemm_f64"}
 PROFILE_EVERY = 8   # events around one launch in 8 of that class (less perturbation of the step)
 # DRAM bytes (read + write) of one k_oz_gemm launch of this workload's shape (300 x 300 x 300,
-# six slices) from an ncu capture (profiles/oz_gemm_emulated_fp64_l300_l1024.md); the
+# six slices) from an ncu capture (profiles/oz_gemm_emulated_fp64_l300_l1024_l2048.md); the
 # algorithmic bytes of that launch (the sliced operands) are 2 x 300 x 6 x 320 x 2 = 2.30 MB
 ROOF_TRAFFIC = {("gemm_oz", "paper_d5_n1000_l300"): 2340096.0}
 
@@ -171,8 +171,9 @@ def main():
                          "App. F, a fixed number of steps per problem; batch: kot_batch_solve "
                          "over an uneven batch (d 2..20, n 200..2000, l 32..512)")
     ap.add_argument("--batch", type=int, default=32, help="problems per batch (--method batch)")
-    ap.add_argument("--no-autotune", action="store_true",
-                    help="skip the (untimed) autotuning of split counts and Jacobi CTAs for l")
+    ap.add_argument("--autotune", action="store_true",
+                    help="run kot_autotune for l first (untimed); off by default: its standalone "
+                         "choices measured no better than the occupancy rule inside the solve")
     ap.add_argument("--max-iter", type=int, default=200,
                     help="outer-iteration cap of Algorithm 2 (lower it to time iterations at large l)")
     ap.add_argument("--workers", type=int, default=8, help="concurrent solves (--method batch)")
@@ -199,9 +200,10 @@ def main():
         return batch_bench(args, world, rank, local_rank, dev)
     p = make_problem(args.workload, rank, 0)
     tuned = None
-    if not args.no_autotune:
+    if args.autotune:
         # untimed: pick the emulated product's split counts and the Jacobi CTA count for this l
-        tuned = dict(zip(("splits_3_slices", "splits_6_slices", "jacobi_ctas"),
+        tuned = dict(zip(("splits_3_slices", "splits_6_slices", "jacobi_ctas", "tile_n_3_slices",
+                          "tile_n_6_slices"),
                          kot.Context(device=local_rank).autotune(p.l)))
     probs = [make_problem(args.workload, rank, k) for k in range(args.steps)]
     dprobs = [kot.DeviceProblem.from_problem(q, dev) for q in probs]

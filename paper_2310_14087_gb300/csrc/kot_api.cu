@@ -1199,23 +1199,28 @@ kot_status kot_autotune(kot_ctx* C, int l, int* choice) {
       KOT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
       return ms / reps;
     };
-    int best_split[2] = {0, 0};
+    int best_split[2] = {0, 0}, best_bn[2] = {64, 64};
     const int slices[2] = {3, 6};
     for (int q = 0; q < 2; ++q) {
       float best = 1e30f;
-      for (int S : {1, 2, 3, 4, 6, 8, 12, 16}) {
-        C->oz.splits_override = S;
-        const float t = timed([&] {
-          gemm_oz(st, C->oz, l, l, l, TcOperand{A.p, l, false, nullptr}, TcOperand{B.p, l, true, nullptr},
-                  slices[q], 1.0, 0.0, Cm.p, l, false);
-        }, 5);
-        if (t < best) {
-          best = t;
-          best_split[q] = S;
+      for (int bn : {64, 128})
+        for (int S : {1, 2, 3, 4, 6, 8, 12, 16}) {
+          C->oz.splits_override = S;
+          C->oz.bn_override = bn;
+          const float t = timed([&] {
+            gemm_oz(st, C->oz, l, l, l, TcOperand{A.p, l, false, nullptr}, TcOperand{B.p, l, true, nullptr},
+                    slices[q], 1.0, 0.0, Cm.p, l, false);
+          }, 5);
+          if (t < best) {
+            best = t;
+            best_split[q] = S;
+            best_bn[q] = bn;
+          }
         }
-      }
       C->oz.splits_override = 0;
+      C->oz.bn_override = 0;
       set_tuned_splits(dev, l, slices[q], best_split[q]);
+      set_tuned_tile_width(dev, l, slices[q], best_bn[q]);
     }
     if (gemm_oz_error(st, C->oz)) fail(KOT_ERR_TIMEOUT, "tensor-core FP64-emulation wait timed out");
     // cooperative Jacobi: CTA count for a cold decomposition of a symmetric l x l matrix
@@ -1240,6 +1245,8 @@ kot_status kot_autotune(kot_ctx* C, int l, int* choice) {
       choice[0] = best_split[0];
       choice[1] = best_split[1];
       choice[2] = best_ctas;
+      choice[3] = best_bn[0];
+      choice[4] = best_bn[1];
     }
     for (DevBuf<double>* b : {&A, &B, &Cm, &P, &sig}) b->release();
   });

@@ -266,6 +266,7 @@ struct OzWork {
   DevBuf<int> err;               // set by a CTA whose bounded wait gave up
   int slices = 6;
   int splits_override = 0;       // > 0: use this split count (the autotuner's probes)
+  int bn_override = 0;           // 64 or 128: use this output-tile width (the autotuner's probes)
   // last TMA descriptors (CUtensorMap, 128 bytes) and the (buffer, rows, cols) they describe
   alignas(64) unsigned char map_a[128], map_b[128];
   const void* key_a = nullptr;
@@ -287,6 +288,8 @@ int gemm_oz_error(cudaStream_t st, OzWork& w);
 // (ceil log2) and slice count (0 = not tuned, use the occupancy rule).
 int tuned_splits(int dev, int mn, int slices);
 void set_tuned_splits(int dev, int mn, int slices, int splits);
+int tuned_tile_width(int dev, int mn, int slices);   // 64, 128 or 0 (not tuned)
+void set_tuned_tile_width(int dev, int mn, int slices, int bn);
 // Autotuner table for the cooperative Jacobi eigensolver: CTAs per size bucket (0 = one per SM).
 int tuned_jacobi_ctas(int dev, int l);
 void set_tuned_jacobi_ctas(int dev, int l, int ctas);

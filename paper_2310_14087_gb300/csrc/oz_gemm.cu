@@ -74,6 +74,7 @@ constexpr int OZ_EXACT_TILES = 8;                // 8 x 64 products of |.| <= 2^
 constexpr int OZ_MAX_SLICES = 8;
 constexpr int OZ_MAX_PAIRS = OZ_MAX_SLICES * (OZ_MAX_SLICES + 1) / 2;
 constexpr int OZ_MAX_SPLITS = 16;
+constexpr int kOzDefaultSplits = 8;
 constexpr int kSplitRows = 16;        // thread rows of a cluster slicing block (32 x 16 threads)
 constexpr int kOzClusterK = 8 * 256;  // K up to which one (portable, <= 8 CTA) cluster spans a row
 
@@ -101,9 +102,10 @@ int sm_count() {
   return cache[dev];
 }
 
-// Split counts chosen by the autotuner, per device, size bucket (ceil log2 of max(M, N)) and
-// slice count; 0 = not tuned.
+// Split counts and tile widths chosen by the autotuner, per device, size bucket (ceil log2 of
+// max(M, N)) and slice count; 0 = not tuned.
 int g_tuned_splits[64][32][OZ_MAX_SLICES + 1] = {};
+int g_tuned_bn[64][32][OZ_MAX_SLICES + 1] = {};
 
 int size_bucket(int mn) {
   int b = 0;
@@ -651,12 +653,17 @@ void gemm_oz(cudaStream_t st, OzWork& w, int M, int N, int K, const TcOperand& A
       ++np;
     }
   P.npairs = np;
-  // wide tiles for large products: twice the MMA work per 64-wide K step for 1.33x the bytes
-  const int BNsel = (M >= 512 && N >= 512) ? 128 : 64;
+  // wide tiles for large products (twice the MMA work per 64-wide K step for 1.33x the bytes),
+  // unless the autotuner chose for this size bucket; w.bn_override (the tuner's probe) wins
+  int BNsel = (M >= 512 && N >= 512) ? 128 : 64;
+  const int tuned_bn = tuned_tile_width(device_index(), std::max(M, N), s);
+  if (tuned_bn == 64 || tuned_bn == 128) BNsel = tuned_bn;
+  if (w.bn_override == 64 || w.bn_override == 128) BNsel = w.bn_override;
   const int tiles = cdiv(N, BNsel) * cdiv(M, OZ_BM);
   // split count: the autotuner's choice for this size bucket and slice count if there is one,
-  // else enough splits to give every SM a CTA; w.splits_override (the tuner's probe) wins
-  int want = std::max(1, nsm / tiles);
+  // else enough splits to give every SM a CTA (at most kOzDefaultSplits, which measured best in
+  // the solve at l = 300); w.splits_override (the tuner's probe) wins
+  int want = std::max(1, std::min(kOzDefaultSplits, nsm / tiles));
   const int tuned = tuned_splits(device_index(), std::max(M, N), s);
   if (tuned > 0) want = tuned;
   if (w.splits_override > 0) want = w.splits_override;
@@ -757,6 +764,16 @@ int tuned_splits(int dev, int mn, int slices) {
 void set_tuned_splits(int dev, int mn, int slices, int splits) {
   if (dev < 0 || dev >= 64 || slices < 0 || slices > OZ_MAX_SLICES) return;
   g_tuned_splits[dev][size_bucket(mn)][slices] = std::max(0, std::min(splits, OZ_MAX_SPLITS));
+}
+
+int tuned_tile_width(int dev, int mn, int slices) {
+  if (dev < 0 || dev >= 64 || slices < 0 || slices > OZ_MAX_SLICES) return 0;
+  return g_tuned_bn[dev][size_bucket(mn)][slices];
+}
+
+void set_tuned_tile_width(int dev, int mn, int slices, int bn) {
+  if (dev < 0 || dev >= 64 || slices < 0 || slices > OZ_MAX_SLICES) return;
+  g_tuned_bn[dev][size_bucket(mn)][slices] = (bn == 64 || bn == 128) ? bn : 0;
 }
 
 int gemm_oz_error(cudaStream_t st, OzWork& w) {

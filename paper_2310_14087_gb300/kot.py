@@ -255,11 +255,12 @@ class Context:
         return self._check(lib().kot_profile(self.h, mask))
 
     def autotune(self, l: int):
-        """Tune the emulated product's split counts and the Jacobi CTA count for size l; returns
-        (splits with 3 slices, splits with 6 slices, Jacobi CTAs)."""
-        out = (C.c_int * 3)()
+        """Tune the emulated product's tile widths and split counts and the Jacobi CTA count for
+        size l; returns (splits 3 slices, splits 6 slices, Jacobi CTAs, width 3 slices,
+        width 6 slices)."""
+        out = (C.c_int * 5)()
         self._check(lib().kot_autotune(self.h, l, out))
-        return out[0], out[1], out[2]
+        return tuple(out)
 
     def profile_every(self, every: int):
         return self._check(lib().kot_profile_every(self.h, every))
