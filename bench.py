@@ -443,68 +443,65 @@ def report(args, probs, world, ms_max, ms_local, stats, launches, iters, conv, c
            e2e, conv_all, tuned=None):
     from paper_2310_14087_gb300 import kot
     value = conv_all / (ms_max / 1e3)          # converged solves per second, all ranks
-    if True:
-        stats, breakdown = stats
-        # the dominant O(l^3) product of the form, timed live with CUDA events in the timed region
-        dom = ROOF_CLASS[args.precision]
-        s = stats[dom]
-        per_launch_ms = s.ms / max(1, s.launches)
-        if s.launches == 0:
-            dom = None
-        if dom is None:
-            pass
-        elif dom == "gemm_oz":
-            # executed BF16 tensor work (slice-pair products) against the sustained BF16 peak
-            bound, unit = "tensor", "TFLOP/s"
-            peak = peaks.get("bf16_tflops_sustained", 1713.0)
-            peak_src = "bf16_tflops_sustained of MEASURED_PEAKS.json (kernel timed inside a long step)"
-        else:
-            bound, unit = "alu", "TFLOP/s"
-            peak, peak_src = FP64_PEAK_TFLOPS, "FP64 FMA: 152 SMs x 2/clk x 2 flop x 2.07 GHz"
-        roofline = None
-        if dom is not None:
-            achieved = (s.flops / s.launches) / (per_launch_ms * 1e-3) / 1e12
-            traffic = ROOF_TRAFFIC.get((dom, args.workload))
-            roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
-                        "unit": unit, "frac": achieved / peak, "traffic": traffic,
-                        "traffic_note": None if traffic is None else
-                        "ncu dram__bytes_read+write of one 300x300x300 six-slice launch (bytes)",
-                        "launches_timed": s.launches, "timed_one_in": PROFILE_EVERY if args.profile == "roofline" else 1,
-                        "avg_launch_us": per_launch_ms * 1e3,
-                        "share_of_step": s.ms * (PROFILE_EVERY if args.profile == "roofline" else 1) / ms_local,
-                        "peak_source": peak_src}
-        line = {
-            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": args.workload, **config_of(args.workload), "tol": 1e-6,
-                       "precision": args.precision, "iters_per_solve": iters,
-                       "converged": sum(conv), "ms_per_iteration": ms_local / max(1, sum(iters)),
-                       "problems": "one seeded problem per step (seed 100 (rank+1) + step)",
-                       "autotuned": tuned,
-                       "l2": "flushed before every step (256 MB write, untimed)"},
-            "other_precision": None if other is None else {
-                "precision": "fp64" if other[0] == kot.FP64 else "mixed", "value": other[1],
-                "ms_per_step": other[2] / args.steps, "iters_per_solve": other[3],
-                "converged": sum(other[4]), "ms_per_iteration": other[2] / max(1, sum(other[3]))},
-            "e2e": e2e,
-            "gpu_launches": launches,
-            "clocks": clocks.summary(),
-            "roofline": roofline,
-            "kernels_one_untimed_step": {k: {"launches": v.launches, "ms": round(v.ms, 3)}
-                                         for k, v in breakdown.items() if v.launches},
-        }
-        if not args.no_cpu_baseline and world == 1:
-            tcpu, r = oracle_solve(probs[0])
-            line["cpu_baseline"] = {
-                "value": (1.0 if r.converged else 0.0) / tcpu, "unit": "solves/s",
-                "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-                "ms_per_iteration": 1e3 * tcpu / max(1, r.iters),
-                "sample": f"1 full solve of {args.workload} (the step-0 problem: features + "
-                          f"Algorithm 2, {r.iters} iterations, converged={r.converged}), "
-                          "NumPy/LAPACK FP64, default BLAS threads"}
-        print(json.dumps(line), flush=True)
+    stats, breakdown = stats
+    # the dominant O(l^3) product of the form, timed live with CUDA events in the timed region
+    dom = ROOF_CLASS[args.precision]
+    s = stats[dom]
+    per_launch_ms = s.ms / max(1, s.launches)
+    if s.launches == 0:
+        dom = None                         # nothing was timed (--profile none)
+    if dom == "gemm_oz":
+        # executed BF16 tensor work (slice-pair products) against the sustained BF16 peak
+        bound, unit = "tensor", "TFLOP/s"
+        peak = peaks.get("bf16_tflops_sustained", 1713.0)
+        peak_src = "bf16_tflops_sustained of MEASURED_PEAKS.json (kernel timed inside a long step)"
+    elif dom is not None:
+        bound, unit = "alu", "TFLOP/s"
+        peak, peak_src = FP64_PEAK_TFLOPS, "FP64 FMA: 152 SMs x 2/clk x 2 flop x 2.07 GHz"
+    roofline = None
+    if dom is not None:
+        achieved = (s.flops / s.launches) / (per_launch_ms * 1e-3) / 1e12
+        traffic = ROOF_TRAFFIC.get((dom, args.workload))
+        roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
+                    "unit": unit, "frac": achieved / peak, "traffic": traffic,
+                    "traffic_note": None if traffic is None else
+                    "ncu dram__bytes_read+write of one 300x300x300 six-slice launch (bytes)",
+                    "launches_timed": s.launches, "timed_one_in": PROFILE_EVERY if args.profile == "roofline" else 1,
+                    "avg_launch_us": per_launch_ms * 1e3,
+                    "share_of_step": s.ms * (PROFILE_EVERY if args.profile == "roofline" else 1) / ms_local,
+                    "peak_source": peak_src}
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, **config_of(args.workload), "tol": 1e-6,
+                   "precision": args.precision, "iters_per_solve": iters,
+                   "converged": sum(conv), "ms_per_iteration": ms_local / max(1, sum(iters)),
+                   "problems": "one seeded problem per step (seed 100 (rank+1) + step)",
+                   "autotuned": tuned,
+                   "l2": "flushed before every step (256 MB write, untimed)"},
+        "other_precision": None if other is None else {
+            "precision": "fp64" if other[0] == kot.FP64 else "mixed", "value": other[1],
+            "ms_per_step": other[2] / args.steps, "iters_per_solve": other[3],
+            "converged": sum(other[4]), "ms_per_iteration": other[2] / max(1, sum(other[3]))},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+        "roofline": roofline,
+        "kernels_one_untimed_step": {k: {"launches": v.launches, "ms": round(v.ms, 3)}
+                                     for k, v in breakdown.items() if v.launches},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        tcpu, r = oracle_solve(probs[0])
+        line["cpu_baseline"] = {
+            "value": (1.0 if r.converged else 0.0) / tcpu, "unit": "solves/s",
+            "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "ms_per_iteration": 1e3 * tcpu / max(1, r.iters),
+            "sample": f"1 full solve of {args.workload} (the step-0 problem: features + "
+                      f"Algorithm 2, {r.iters} iterations, converged={r.converged}), "
+                      "NumPy/LAPACK FP64, default BLAS threads"}
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -27,14 +27,24 @@
 // Net accuracy: about 2^-47 relative to max_k |A(r,k)| * max_k |B(c,k)| * K per element for
 // s = 6, i.e. FP64 GEMM accuracy up to a small factor.
 //
-// Kernels: (1) per-row exponent partials, (2) slicing into a BF16 operand matrix [rows][s * Kp]
-// (slice i occupies columns i * Kp .. i * Kp + Kp - 1), (3) the tcgen05 GEMM: one CTA per
-// 128 x 64 output tile and split z of the slice pairs; warp 4 streams 128 x 64 (A) and 64 x 64
-// (B) BF16 tiles with TMA into a 6-stage ring, warp 5 issues tcgen05.mma (M 128, N 64, K 16)
-// into one of two 64-column FP32 accumulators in tensor memory and hands each finished group
-// to warps 0-3, which drain it while the next group accumulates in the other buffer; the
-// (hi, lo) pairs of each split go to a float2 buffer; (4) finalize: sum the splits, convert to
-// FP64, scale by alpha 2^(e_r - 7) 2^(e_c - 7), add beta C.  Every wait is bounded.
+// Kernels:
+// (1) slicing into a BF16 operand matrix [rows][s * Kp] (slice i occupies columns i * Kp ..
+//     i * Kp + Kp - 1). For K <= 2048 one launch: a thread-block cluster of <= 8 CTAs spans the K
+//     range of 32 rows and exchanges per-row exponents through distributed shared memory. For
+//     larger K, an exponent-partials kernel and a slicing kernel.
+// (2) the tcgen05 GEMM, one CTA per output tile (128 x 64, or 128 x 128 when M, N >= 512) and
+//     split z of the (slice pair, k tile) sequence:
+//     * the TMA producer warp streams 128 x 64 (A) and BN x 64 (B) BF16 tiles into a 6-stage
+//       ring;
+//     * the MMA warp issues tcgen05.mma (M 128, N BN, K 16) into one of two BN-column FP32
+//       accumulators in tensor memory and hands each finished group to the BN / 16 epilogue
+//       warps (64 columns each), which drain it while the next group accumulates in the other
+//       buffer;
+//     * the (hi, lo) pairs of each split go, staged through the free operand ring, to a float2
+//       buffer.
+// (3) finalize: sum the splits, convert to FP64, scale by alpha 2^(e_r - 7) 2^(e_c - 7), add
+//     beta C.
+// Every wait is bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
