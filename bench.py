@@ -50,11 +50,31 @@ PROFILE_EVERY = 8   # events around one launch in 8 of that class (less perturba
 ROOF_TRAFFIC = {("gemm_oz", "paper_d5_n1000_l300"): 2340096.0}
 
 
+def seed_of(rank: int, step: int) -> int:
+    """Seed of the problem solved in `step` by `rank` (step < 0: warm-up problems); every rank
+    solves problems of its own (weak scaling: no problem is shared or split across ranks)."""
+    return 100 * (rank + 1) + step if step >= 0 else 10_000 + 100 * rank - step
+
+
 def make_problem(name: str, rank: int, step: int = 0):
     """Problem solved in `step` by `rank` (step < 0: warm-up problems)."""
     cfg = WORKLOADS[name]
-    seed = 100 * (rank + 1) + step if step >= 0 else 10_000 + 100 * rank - step
-    return workloads.paper_regime(seed=seed, d=cfg["d"], n=cfg["n"], l=cfg["l"])
+    return workloads.paper_regime(seed=seed_of(rank, step), d=cfg["d"], n=cfg["n"], l=cfg["l"])
+
+
+def job_totals(count_local: float, ms_local: float, world: int, device="cpu"):
+    """Whole-job aggregate over the ranks of the default process group: (units summed over ranks,
+    time = max over ranks in ms, rate = units / max time in s).  This reduction and the barriers
+    around the timed region are the only cross-rank traffic."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    c = torch.tensor([float(count_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c)
+    ms, units = float(t.item()), float(c.item())
+    return units, ms, units / (ms / 1e3) if ms > 0 else 0.0
 
 
 def config_of(name: str) -> dict:
@@ -261,24 +281,16 @@ def main():
         torch.cuda.synchronize()
         breakdown = {name: ctx.profile_read(i) for i, name in enumerate(kot.KERNEL_CLASSES)}
         ctx.profile(0)
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item()), ms, (stats, breakdown), launches, iters, conv
+        return ms, (stats, breakdown), launches, iters, conv
 
     main_prec = kot.MIXED if args.precision == "mixed" else kot.FP64
     other_prec = kot.FP64 if main_prec == kot.MIXED else kot.MIXED
     with ClockSampler(local_rank) as clocks:
-        ms_max, ms_local, stats, launches, iters, conv = timed(main_prec)
-    conv_all = torch.tensor([float(sum(conv))], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(conv_all)
+        ms_local, stats, launches, iters, conv = timed(main_prec)
+    conv_all, ms_max, _ = job_totals(sum(conv), ms_local, world, dev)
     if not args.skip_other:
-        o_ms_max, _, o_stats, _, o_iters, o_conv = timed(other_prec)
-        o_conv_all = torch.tensor([float(sum(o_conv))], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(o_conv_all)
-        o_value = float(o_conv_all.item()) / (o_ms_max / 1e3)
+        o_ms_local, _, _, o_iters, o_conv = timed(other_prec)
+        _, o_ms_max, o_value = job_totals(sum(o_conv), o_ms_local, world, dev)
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
@@ -287,7 +299,7 @@ def main():
     if rank == 0:
         report(args, probs, world, ms_max, ms_local, stats, launches, iters, conv, clocks, peaks,
                None if args.skip_other else (other_prec, o_value, o_ms_max, o_iters, o_conv), e2e,
-               float(conv_all.item()), tuned)
+               conv_all, tuned)
     if world > 1:
         dist.destroy_process_group()
 
