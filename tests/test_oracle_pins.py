@@ -406,6 +406,20 @@ def test_potential_gradient_and_map():
     np.testing.assert_allclose(u0, emb / (2 * p.lambda2), rtol=1e-13)
 
 
+def test_estimator_near_closed_form_gaussian_w2():
+    # loose statistical sanity check (not a parity gate): for mu = N(0, I_2), nu = N((1,1),
+    # diag(0.5, 2)) the estimator targets W2^2/2 = (|m1 - m2|^2 + tr(S1 + S2 - 2 (S2^1/2 S1
+    # S2^1/2)^1/2))/2 = (2 + (1 - sqrt .5)^2 + (1 - sqrt 2)^2)/2 = 1.1287; with the paper's
+    # lambda2 = 1/sqrt(n) (Sec. 3 remark) at n = 100, l = 50 the estimate at the optimum (taken
+    # from the independent interior-point solve) lands within a factor 1.5 of it
+    half_w2 = 0.5 * (2.0 + (1 - math.sqrt(0.5)) ** 2 + (1 - math.sqrt(2.0)) ** 2)
+    p = wl.gaussian_pair(n=100, l=50, lambda2=0.1, lambda1=1e-3)
+    F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
+    g, _ = ind.ipm_solve(F.Q, F.z, F.q2, F.R, F.lambda1, F.lambda2)
+    est = ko.ot_estimate(F, g)
+    assert half_w2 / 1.5 < est < 1.5 * half_w2
+
+
 # ---------------------------------------------------------------- planted mistakes
 def test_planted_mistakes_are_caught(monkeypatch):
     """Each mutation reproduces a plausible slip; the pin named beside it must reject it."""
