@@ -69,6 +69,8 @@ struct kot_ctx {
   EigSlot ew, ev, et, e1, e2;
   DevBuf<double> M1, M2, M3, M4, M5, M6, TU, TV, TW, TG;
   DevBuf<double> v1, v2, v3, v4, v5, v6, w1, w2, w3;
+  DevBuf<double> Fvg, FvX;     // F(v) of the EG iterate, from its last residual evaluation
+  bool fv_valid = false;
   DevBuf<double> partial, scal, bounds;
   DevBuf<int> iscal;
   double* hs = nullptr;                        // pinned host scalars
@@ -128,8 +130,9 @@ void ensure(kot_ctx* C, int l) {
   const size_t L2 = (size_t)l * l, L = (size_t)l;
   for (DevBuf<double>* b : {&C->Q, &C->K, &C->R, &C->X, &C->vX, &C->tX, &C->dX, &C->M1, &C->M2,
                             &C->M3, &C->M4, &C->M5, &C->M6, &C->TU, &C->TV, &C->TW, &C->TG,
-                            &C->rw.r2, &C->rv.r2, &C->rt.r2})
+                            &C->rw.r2, &C->rv.r2, &C->rt.r2, &C->FvX})
     b->alloc(L2);
+  C->Fvg.alloc(L);
   for (DevBuf<double>* b : {&C->z, &C->w_mu, &C->w_nu, &C->c, &C->g, &C->vg, &C->tg, &C->dg,
                             &C->v1, &C->v2, &C->v3, &C->v4, &C->v5, &C->v6, &C->w1, &C->w2,
                             &C->w3, &C->rw.r1,
@@ -267,11 +270,17 @@ void proj_inplace(kot_ctx* C, double* M, EigSlot& e) {
 }
 
 // R(w) of Eq. (4.2) into r; eigen-decomposition of Z(w) into e.
+// save_fv: (gamma, X) is the EG iterate v; keep F(v) = (r1, Phi*(gamma) + lambda1 I) for the next
+// extragradient step, which starts by evaluating exactly these (same kernels, same bits).
 void residual(kot_ctx* C, const double* gamma, const double* X, EigSlot& e, const EigSlot* warm,
-              ResState& r) {
+              ResState& r, bool save_fv = false) {
   const int l = C->l;
   const size_t L2 = (size_t)l * l;
   phi_star(C, gamma, C->M1.p);
+  if (save_fv) {
+    copy_mat(C->st, l, l, C->M1.p, l, C->FvX.p, l);
+    add_diag(C->st, l, C->lambda1, C->FvX.p, l);               // F_X(v) = Phi*(gamma) + lambda1 I
+  }
   axpby(C->st, L2, 1.0, X, -1.0, C->M1.p, C->M1.p);          // Z = X - Phi*(gamma)
   add_diag(C->st, l, -C->lambda1, C->M1.p, l);                // ... - lambda1 I
   symmetrize(C->st, l, C->M1.p);
@@ -279,6 +288,10 @@ void residual(kot_ctx* C, const double* gamma, const double* X, EigSlot& e, cons
   form_proj(C, C->M1.p, e, C->M2.p);
   axpby(C->st, L2, 1.0, X, -1.0, C->M2.p, r.r2.p);            // r2 = X - Pi(Z)
   grad_gamma(C, gamma, X, r.r1.p, C->v1.p, C->M3.p);           // r1
+  if (save_fv) {
+    KOT_CUDA(cudaMemcpyAsync(C->Fvg.p, r.r1.p, l * sizeof(double), cudaMemcpyDeviceToDevice, C->st));
+    C->fv_valid = true;                                       // F_gamma(v) = r1(v)
+  }
   sumsq_f64(C->st, l, r.r1.p, C->scal.p, C->partial.p);
   sumsq_f64(C->st, L2, r.r2.p, C->scal.p + 1, C->partial.p);
   fetch(C, 2);
@@ -512,12 +525,18 @@ void eg_step(kot_ctx* C, double eta) {
   const int l = C->l;
   const size_t L2 = (size_t)l * l;
   cudaStream_t st = C->st;
-  // F at v
-  grad_gamma(C, C->vg.p, C->vX.p, C->v2.p, C->v1.p, C->M3.p);    // v2 = F_gamma(v)
-  phi_star(C, C->vg.p, C->M1.p);
-  add_diag(st, l, C->lambda1, C->M1.p, l);                        // M1 = F_X(v)
+  // F at v (kept from the residual of v when that was the last thing computed at v)
+  const double* FX = C->M1.p;
+  if (C->fv_valid) {
+    KOT_CUDA(cudaMemcpyAsync(C->v2.p, C->Fvg.p, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    FX = C->FvX.p;
+  } else {
+    grad_gamma(C, C->vg.p, C->vX.p, C->v2.p, C->v1.p, C->M3.p);  // v2 = F_gamma(v)
+    phi_star(C, C->vg.p, C->M1.p);
+    add_diag(st, l, C->lambda1, C->M1.p, l);                      // M1 = F_X(v)
+  }
   axpby(st, l, 1.0, C->vg.p, -eta, C->v2.p, C->v4.p);             // gamma_h
-  axpby(st, L2, 1.0, C->vX.p, -eta, C->M1.p, C->M2.p);            // X_v - eta F_X(v)
+  axpby(st, L2, 1.0, C->vX.p, -eta, FX, C->M2.p);                 // X_v - eta F_X(v)
   proj_inplace(C, C->M2.p, C->e1);                                // X_h
   // F at h
   grad_gamma(C, C->v4.p, C->M2.p, C->v3.p, C->v1.p, C->M3.p);
@@ -526,6 +545,7 @@ void eg_step(kot_ctx* C, double eta) {
   axpby(st, l, 1.0, C->vg.p, -eta, C->v3.p, C->vg.p);
   axpby(st, L2, 1.0, C->vX.p, -eta, C->M1.p, C->vX.p);
   proj_inplace(C, C->vX.p, C->e2);
+  C->fv_valid = false;                                            // v has moved
 }
 
 double pair_inner(kot_ctx* C, const ResState& r, const double* dg, const double* dX) {
@@ -598,6 +618,7 @@ void factor(kot_ctx* C) {
 
 void reset_slots(kot_ctx* C) {
   for (EigSlot* e : {&C->ew, &C->ev, &C->et, &C->e1, &C->e2}) e->valid = false;
+  C->fv_valid = false;
 }
 
 }  // namespace
@@ -687,7 +708,7 @@ kot_status kot_destroy(kot_ctx* C) {
                             &C->w3, &C->partial,
                             &C->scal, &C->bounds, &C->rw.r1, &C->rw.r2, &C->rv.r1, &C->rv.r2,
                             &C->rt.r1, &C->rt.r2, &C->eZ, &C->eP, &C->esig, &C->sX, &C->sY,
-                            &C->sXf, &C->sYf})
+                            &C->sXf, &C->sYf, &C->Fvg, &C->FvX})
     b->release();
   C->jw.release();
   C->tc.a.release();
@@ -958,7 +979,7 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
     while (C->rw.norm > tol && it < o.max_iter) {
       if (o.use_eg) {
         eg_step(C, eta);
-        residual(C, C->vg.p, C->vX.p, C->ev, &C->ev, C->rv);
+        residual(C, C->vg.p, C->vX.p, C->ev, &C->ev, C->rv, true);
       }
       const double mu = theta * C->rw.norm;
       // mixed form: tensor-core products far from the solution, FP64 near it
@@ -1064,14 +1085,14 @@ kot_status kot_eg_solve(kot_ctx* C, double tol, double* gamma_out, double* X_out
       fill(st, L2, 0.0, C->vX.p);
     }
     const double eta = o.eg_step > 0 ? o.eg_step : 1.0 / C->eg_L;
-    residual(C, C->vg.p, C->vX.p, C->ev, nullptr, C->rv);
+    residual(C, C->vg.p, C->vX.p, C->ev, nullptr, C->rv, true);
     C->hist.clear();
     C->trace.clear();
     if (o.record_history) C->hist.push_back(C->rv.norm);
     int it = 0;
     while (C->rv.norm > tol && it < o.max_iter) {
       eg_step(C, eta);
-      residual(C, C->vg.p, C->vX.p, C->ev, &C->ev, C->rv);
+      residual(C, C->vg.p, C->vX.p, C->ev, &C->ev, C->rv, true);
       ++it;
       if (o.record_history) C->hist.push_back(C->rv.norm);
     }
