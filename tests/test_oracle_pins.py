@@ -325,6 +325,28 @@ def test_kkt_invariants_at_solution():
     assert np.linalg.norm(r1) <= tol
 
 
+def test_primal_dual_gap_closes_at_solution():
+    # Lagrangian of Eq. (3.3) with multiplier X for the PSD constraint: minimising over gamma
+    # (Q > 0) gives the dual function g(X) = q^2/(4 l2) - l1 tr X - b^T Q^-1 b/(4 l2),
+    # b = z + 2 l2 Phi(X); weak duality f(gamma) >= g(X) holds for every X >= 0, and at a
+    # solution (R(w) = 0) the gap f - g = <X, Phi*(gamma) + l1 I> closes (strong duality)
+    F = _small_features(seed=0, l=8, sigma=0.35)
+    r = ko.ssn_solve(F, 1e-10, ko.Options(max_iter=500))
+    assert r.converged
+
+    def g_dual(X):
+        b = F.z + 2 * F.lambda2 * ko.phi(F.R, X)
+        return F.q2 / (4 * F.lambda2) - F.lambda1 * np.trace(X) - b @ np.linalg.solve(F.Q, b) / (4 * F.lambda2)
+
+    f = ko.objective(F, r.gamma)
+    assert f - g_dual(r.X) == pytest.approx(0.0, abs=1e-8 * max(1.0, abs(f)))
+    # weak duality at other PSD points (the dual function lies below the primal optimum)
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        A = rng.standard_normal((F.l, F.l))
+        assert g_dual(0.1 * A @ A.T) <= f + 1e-10
+
+
 def test_golden_algorithm_constants():
     g = json.load(open(os.path.join(GOLDEN, "algorithm_constants.json")))
     o = ko.Options()
