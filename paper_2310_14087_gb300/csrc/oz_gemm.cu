@@ -55,6 +55,7 @@
 #include <cstring>
 
 #include "kot_internal.cuh"
+#include "oz_slicing.cuh"
 #include "tc_ptx.cuh"
 
 namespace kot {
@@ -79,9 +80,9 @@ struct OzCfg {
   static constexpr int TMEM_COLS = 2 * BN;                  // two accumulator buffers
   static_assert(EPI * 32 * 65 * 8 <= OZ_STAGES * STAGE, "epilogue staging fits in the ring");
 };
-constexpr int OZ_EXACT_LEVELS = 4;
-constexpr int OZ_EXACT_TILES = 8;                // 8 x 64 products of |.| <= 2^14: sum <= 2^23
-constexpr int OZ_MAX_SLICES = 8;
+constexpr int OZ_EXACT_LEVELS = oz::kExactLevels;
+constexpr int OZ_EXACT_TILES = oz::kExactTiles;
+constexpr int OZ_MAX_SLICES = oz::kMaxSlices;
 constexpr int OZ_MAX_PAIRS = OZ_MAX_SLICES * (OZ_MAX_SLICES + 1) / 2;
 constexpr int OZ_MAX_SPLITS = 16;
 constexpr int kOzDefaultSplits = 8;
@@ -131,13 +132,7 @@ struct OzPlan {
   int* err;
 };
 
-// Does the tile of level lv (following a tile of level prev; gt tiles already in the current
-// group) start a new accumulation group?
-__device__ __forceinline__ bool oz_new_group(int prev, int lv, int gt) {
-  if (gt == 0) return true;
-  if (lv != prev && (lv < OZ_EXACT_LEVELS || prev < OZ_EXACT_LEVELS)) return true;
-  return lv < OZ_EXACT_LEVELS && gt >= OZ_EXACT_TILES;
-}
+__device__ __forceinline__ bool oz_new_group(int prev, int lv, int gt) { return oz::new_group(prev, lv, gt); }
 
 // (hi, lo) += g with Knuth's error-free two-sum on hi; rounding is pinned (no contraction).
 __device__ __forceinline__ void ff_add(float& hi, float& lo, float g) {
@@ -348,9 +343,7 @@ struct OzSplitArgs {
   int Kp, s;
 };
 
-__device__ __forceinline__ int biased_exp(double v) {
-  return (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FFu);
-}
+__device__ __forceinline__ int biased_exp(double v) { return oz::biased_exp(v); }
 
 __device__ __forceinline__ double oz_load(const OzOperand& o, int r, int k) {
   double v = o.trans ? o.src[(size_t)k * o.ld + r] : o.src[(size_t)r * o.ld + k];
@@ -396,37 +389,8 @@ __global__ void k_oz_rowexp(OzSplitArgs a) {
   }
 }
 
-// Balanced base-256 digits of v relative to the row exponent er (max |v| < 2^er):
-// |v| 2^(7 + 8 (s-1) - er) rounded to the integer X = sum_i d_i 256^(s-1-i), |d_i| <= 128.
-// Integer arithmetic only (FP64 issue is scarce on this part).
 __device__ __forceinline__ void oz_digits(double v, int er, int s, int (&d)[OZ_MAX_SLICES]) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  int E = (int)((b >> 52) & 0x7FFu);
-  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-  if (E == 0) E = 1;             // subnormal: no implicit bit
-  else m |= 1ull << 52;          // |v| = m 2^(E - 1075)
-  const int sh = 1075 - E - 7 - 8 * (s - 1) + er;
-  unsigned long long X;
-  if (sh >= 64) X = 0;
-  else if (sh > 0) X = (m >> sh) + ((m >> (sh - 1)) & 1ull);
-  else X = m << (-sh);
-#pragma unroll
-  for (int i = OZ_MAX_SLICES - 1; i >= 1; --i) {
-    d[i] = 0;
-    if (i < s) {
-      int dd = (int)(X & 0xFFu);
-      X >>= 8;
-      if (dd >= 128) {
-        dd -= 256;
-        ++X;
-      }
-      d[i] = dd;
-    }
-  }
-  d[0] = (int)X;
-  if (b >> 63)
-#pragma unroll
-    for (int i = 0; i < OZ_MAX_SLICES; ++i) d[i] = -d[i];
+  oz::digits(v, er, s, d);
 }
 
 // Slicing for K > kOzClusterK: row exponents from the partials of k_oz_rowexp.
