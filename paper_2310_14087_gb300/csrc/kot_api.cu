@@ -27,6 +27,7 @@ struct EigSlot {
   DevBuf<double> P, sig;
   int nb = 0;          // number of eigenvalues <= 0 (alpha-bar); alpha = the last l - nb
   bool valid = false;
+  bool trivial = false;   // came from an exactly diagonal matrix (identity basis): no use as a warm start
 };
 
 struct ResState {
@@ -71,6 +72,8 @@ struct kot_ctx {
   DevBuf<double> v1, v2, v3, v4, v5, v6, w1, w2, w3;
   DevBuf<double> Fvg, FvX;     // F(v) of the EG iterate, from its last residual evaluation
   bool fv_valid = false;
+  DevBuf<double> Plast;        // most recent non-trivial eigenbasis of the running solve
+  bool plast_valid = false, in_solve = false;
   DevBuf<double> partial, scal, bounds;
   DevBuf<int> iscal;
   double* hs = nullptr;                        // pinned host scalars
@@ -130,7 +133,7 @@ void ensure(kot_ctx* C, int l) {
   const size_t L2 = (size_t)l * l, L = (size_t)l;
   for (DevBuf<double>* b : {&C->Q, &C->K, &C->R, &C->X, &C->vX, &C->tX, &C->dX, &C->M1, &C->M2,
                             &C->M3, &C->M4, &C->M5, &C->M6, &C->TU, &C->TV, &C->TW, &C->TG,
-                            &C->rw.r2, &C->rv.r2, &C->rt.r2, &C->FvX})
+                            &C->rw.r2, &C->rv.r2, &C->rt.r2, &C->FvX, &C->Plast})
     b->alloc(L2);
   C->Fvg.alloc(L);
   for (DevBuf<double>* b : {&C->z, &C->w_mu, &C->w_nu, &C->c, &C->g, &C->vg, &C->tg, &C->dg,
@@ -227,7 +230,12 @@ void grad_gamma(kot_ctx* C, const double* gamma, const double* X, double* out, d
 // alpha-bar count back to the host.
 void eig_into(kot_ctx* C, const double* Z, EigSlot& e, const EigSlot* warm) {
   const int l = C->l;
-  const double* wp = (warm && warm->valid) ? warm->P.p : nullptr;
+  // Warm start: the previous basis of the same sequence; inside a solve, when that is missing or
+  // only the identity of a diagonal matrix (the start, w0 = v0 = 0), the most recent non-trivial
+  // basis of any sequence (e.g. R(v1) from the EG projection just computed) -- refinement falls
+  // back to Jacobi sweeps when it is too far off.
+  const double* wp = (warm && warm->valid && !warm->trivial) ? warm->P.p : nullptr;
+  if (!wp && C->in_solve && C->plast_valid) wp = C->Plast.p;
   // Mixed form: a refinement whose correction is <= 1e-6 leaves a basis accurate to ~1e-12,
   // below the accuracy of its emulated products; the eigenvalues (Rayleigh quotients, which decide
   // alpha and Omega) are accurate to second order.  The FP64 form refines to FP64 rounding.
@@ -242,6 +250,11 @@ void eig_into(kot_ctx* C, const double* Z, EigSlot& e, const EigSlot* warm) {
   KOT_CUDA(cudaStreamSynchronize(C->st));
   e.nb = C->hi[0];
   e.valid = true;
+  e.trivial = wp == nullptr && C->jw.last_sweeps == 0 && C->jw.last_refine == 0;
+  if (C->in_solve && !e.trivial) {
+    KOT_CUDA(cudaMemcpyAsync(C->Plast.p, e.P.p, (size_t)l * l * sizeof(double), cudaMemcpyDeviceToDevice, C->st));
+    C->plast_valid = true;
+  }
 }
 
 // out = Pi_{S+}(Z) from slot e (Eq. (4.4)); out may alias Z.
@@ -563,6 +576,7 @@ void swap_slots(EigSlot& a, EigSlot& b) {
   std::swap(a.sig, b.sig);
   std::swap(a.nb, b.nb);
   std::swap(a.valid, b.valid);
+  std::swap(a.trivial, b.trivial);
 }
 void swap_res(ResState& a, ResState& b) {
   std::swap(a.r1, b.r1);
@@ -617,8 +631,9 @@ void factor(kot_ctx* C) {
 }
 
 void reset_slots(kot_ctx* C) {
-  for (EigSlot* e : {&C->ew, &C->ev, &C->et, &C->e1, &C->e2}) e->valid = false;
+  for (EigSlot* e : {&C->ew, &C->ev, &C->et, &C->e1, &C->e2}) e->valid = e->trivial = false;
   C->fv_valid = false;
+  C->plast_valid = false;
 }
 
 }  // namespace
@@ -633,6 +648,7 @@ kot_status run(kot_ctx* C, const std::function<void()>& body) {
   } install(C);
   if (C) {
     C->force64 = false;
+    C->in_solve = false;
     C->jw.oz = C->opt.precision == KOT_MIXED ? &C->oz : nullptr;
   }
   try {
@@ -708,7 +724,7 @@ kot_status kot_destroy(kot_ctx* C) {
                             &C->w3, &C->partial,
                             &C->scal, &C->bounds, &C->rw.r1, &C->rw.r2, &C->rv.r1, &C->rv.r2,
                             &C->rt.r1, &C->rt.r2, &C->eZ, &C->eP, &C->esig, &C->sX, &C->sY,
-                            &C->sXf, &C->sYf, &C->Fvg, &C->FvX})
+                            &C->sXf, &C->sYf, &C->Fvg, &C->FvX, &C->Plast})
     b->release();
   C->jw.release();
   C->tc.a.release();
@@ -954,6 +970,7 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
     cudaStream_t st = C->st;
     const kot_options& o = C->opt;
     reset_slots(C);
+    C->in_solve = true;   // cross-sequence warm starts (eig_into) within this solve
     C->eig_calls = C->eig_sweeps = C->eig_refined = C->eig_refine_steps = 0;
     if (gamma0) {
       const double* p = dev_in(C, 0, gamma0, l);
@@ -1011,6 +1028,7 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
         KOT_CUDA(cudaMemcpyAsync(C->ev.sig.p, C->ew.sig.p, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
         C->ev.nb = C->ew.nb;
         C->ev.valid = true;
+        C->ev.trivial = C->ew.trivial;
         ++egt;
       }
       ++it;
@@ -1071,6 +1089,7 @@ kot_status kot_eg_solve(kot_ctx* C, double tol, double* gamma_out, double* X_out
     cudaStream_t st = C->st;
     const kot_options& o = C->opt;
     reset_slots(C);
+    C->in_solve = true;   // cross-sequence warm starts (eig_into) within this solve
     C->eig_calls = C->eig_sweeps = C->eig_refined = C->eig_refine_steps = 0;
     if (gamma0) {
       const double* p = dev_in(C, 0, gamma0, l);
