@@ -276,6 +276,14 @@ kot_status kot_profile_every(kot_ctx* ctx, int every);
 kot_status kot_launch_count(long long* out);
 kot_status kot_profile_read(kot_ctx* ctx, int cls, kot_kernel_stats* out);
 
+/* ---- failure detection self-test (not part of the paper's method) ----
+ * Launches a kernel that waits, with the bounded poll every tensor-core pipeline wait uses, on an
+ * mbarrier that nothing completes; after `polls` polls (1..1e8, each at least 20 ns) it gives up,
+ * sets the error flag, and returns.  The call therefore returns KOT_ERR_TIMEOUT -- the status a
+ * starved pipeline stage turns into -- and leaves the context usable.  KOT_ERR_INVALID for polls
+ * out of range. */
+kot_status kot_wait_probe(kot_ctx* ctx, long long polls);
+
 /* ---- allocation-free entry point (the paper has no counterpart; an interface addition) ----
  * ||w||^2 = (1/n^2) sum_{i,j} exp(-||s_i - s_j||^2 / (2 sigma^2)) over the n x d samples S (one
  * half of q2 in kot_build_features), for callers that must not allocate device memory while

@@ -13,9 +13,19 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kot_internal.cuh"
 
 using namespace kot;
+
+namespace {
+// NVTX range for the phases of a solve (visible to Nsight tools, free otherwise)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+}  // namespace
 
 // layouts the ctypes binding mirrors (LP64, natural alignment)
 static_assert(sizeof(kot_options) == 176, "kot_options layout");
@@ -229,6 +239,7 @@ void grad_gamma(kot_ctx* C, const double* gamma, const double* X, double* out, d
 // Eigen-decompose Z (read only) into slot e (warm-started from `warm` if valid); reads the
 // alpha-bar count back to the host.
 void eig_into(kot_ctx* C, const double* Z, EigSlot& e, const EigSlot* warm) {
+  Range range("kot/eig");
   const int l = C->l;
   // Warm start: the previous basis of the same sequence; inside a solve, when that is missing or
   // only the identity of a diagonal matrix (the start, w0 = v0 = 0), the most recent non-trivial
@@ -287,6 +298,7 @@ void proj_inplace(kot_ctx* C, double* M, EigSlot& e) {
 // extragradient step, which starts by evaluating exactly these (same kernels, same bits).
 void residual(kot_ctx* C, const double* gamma, const double* X, EigSlot& e, const EigSlot* warm,
               ResState& r, bool save_fv = false) {
+  Range range("kot/residual");
   const int l = C->l;
   const size_t L2 = (size_t)l * l;
   phi_star(C, gamma, C->M1.p);
@@ -438,6 +450,7 @@ int sqmr_loop(kot_ctx* C, const ResState& r, const EigSlot& e, double mu, double
 // rule multiplies theta by beta2, and convergence turns linear.
 int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu, double cg_tol_abs,
                      double* dgam, double* dX, bool allow_tc) {
+  Range range("kot/newton_direction");
   const int l = C->l;
   C->force64 = !allow_tc;
   const size_t L2 = (size_t)l * l;
@@ -535,6 +548,7 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
 
 // One projected extragradient step on (vg, vX) with step eta (Korpelevich).
 void eg_step(kot_ctx* C, double eta) {
+  Range range("kot/eg_step");
   const int l = C->l;
   const size_t L2 = (size_t)l * l;
   cudaStream_t st = C->st;
@@ -757,6 +771,7 @@ kot_status kot_build_features(kot_ctx* C, int d, int n, const double* X, const d
     return KOT_ERR_INVALID;
   }
   return run(C, [&] {
+    Range range("kot/build_features");
     KOT_CUDA(cudaSetDevice(C->opt.device));
     C->have = false;
     C->have_samples = false;
@@ -1328,6 +1343,19 @@ kot_status kot_dense_product(kot_ctx* C, int M, int N, int K, double alpha, cons
     if (pieces > 0 && gemm_tc_error(C->st, C->tc)) fail(KOT_ERR_TIMEOUT, "tensor-core GEMM wait timed out");
     if (pieces < 0 && gemm_oz_error(C->st, C->oz)) fail(KOT_ERR_TIMEOUT, "tensor-core GEMM wait timed out");
   });
+}
+
+kot_status kot_wait_probe(kot_ctx* C, long long polls) {
+  if (!C) return KOT_ERR_INVALID;
+  if (polls < 1 || polls > 100000000LL) {
+    C->err = "kot_wait_probe: polls must be in 1..1e8";
+    return KOT_ERR_INVALID;
+  }
+  kot_status s = run(C, [&] {
+    KOT_CUDA(cudaSetDevice(C->opt.device));
+    if (starved_wait_probe(C->st, C->tc, polls)) fail(KOT_ERR_TIMEOUT, "bounded device wait gave up (probe)");
+  });
+  return s;
 }
 
 kot_status kot_launch_count(long long* out) {

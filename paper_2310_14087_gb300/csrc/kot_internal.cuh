@@ -252,6 +252,9 @@ void gemm_tc(cudaStream_t st, TcWork& w, int M, int N, int K, const TcOperand& A
              const TcOperand& B, int pieces, double alpha, double beta, double* C, int ldc);
 // Nonzero if a tensor-core GEMM CTA timed out since the last call (clears the flag).
 int gemm_tc_error(cudaStream_t st, TcWork& w);
+// Launch a kernel whose bounded mbarrier wait nothing completes (polls >= 1); returns the
+// error flag it leaves (1: the wait gave up, as it must).
+int starved_wait_probe(cudaStream_t st, TcWork& w, long long polls);
 
 // ------------------------------------------------------------------ FP64 emulation (oz_gemm.cu)
 // FP64-accurate C (M x N, ldc) = alpha * sum_k opA(r=m, k) opB(r=n, k) + beta * C on the tensor

@@ -262,6 +262,33 @@ void gemm_tc(cudaStream_t st, TcWork& w, int M, int N, int K, const TcOperand& A
   KOT_LAUNCHED(1);
 }
 
+namespace {
+// Failure-detection probe: one thread waits, with the same bounded poll as the tensor-core
+// kernels, on an mbarrier that expects one arrival nobody makes; when the polls run out it records
+// the timeout in *err, exactly as a starved pipeline stage would, and the kernel returns.
+__global__ void k_starved_wait(long long polls, int* __restrict__ err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  for (long long i = 0; i < polls; ++i) {
+    if (mbar_try_wait(&bar, 0)) return;   // never: nothing arrives
+    __nanosleep(20);
+  }
+  atomicExch(err, 1);
+}
+}  // namespace
+
+int starved_wait_probe(cudaStream_t st, TcWork& w, long long polls) {
+  if (!w.err.p) {
+    w.err.alloc(1);
+    KOT_CUDA(cudaMemsetAsync(w.err.p, 0, sizeof(int), st));
+  }
+  k_starved_wait<<<1, 32, 0, st>>>(polls, w.err.p);
+  KOT_CHECK_LAUNCH();
+  return gemm_tc_error(st, w);
+}
+
 int gemm_tc_error(cudaStream_t st, TcWork& w) {
   if (!w.err.p) return 0;
   int h = 0;

@@ -61,7 +61,7 @@ EXPORTS = ["kot_default_options", "kot_create", "kot_destroy", "kot_last_error",
            "kot_newton_direction", "kot_ssn_solve", "kot_get_history", "kot_batch_solve",
            "kot_profile", "kot_profile_read", "kot_launch_count",
            "kot_embedding_sqnorm_noalloc", "kot_dense_product", "kot_get_trace", "kot_eig_sym",
-           "kot_eg_solve", "kot_potentials", "kot_profile_every", "kot_autotune"]
+           "kot_eg_solve", "kot_potentials", "kot_profile_every", "kot_autotune", "kot_wait_probe"]
 
 KERNEL_CLASSES = ["gemm_f64", "jacobi_f64", "jacobi_f32", "embed", "pair_sums", "gram",
                   "cholesky", "gemm_tc", "eig_refine", "gemm_oz", "oz_aux"]
@@ -99,6 +99,7 @@ def lib() -> C.CDLL:
         "kot_profile": (i, [vp, i]),
         "kot_profile_every": (i, [vp, i]),
         "kot_autotune": (i, [vp, i, vp]),
+        "kot_wait_probe": (i, [vp, C.c_longlong]),
         "kot_profile_read": (i, [vp, i, C.POINTER(KernelStats)]),
         "kot_launch_count": (i, [C.POINTER(C.c_longlong)]),
         "kot_dense_product": (i, [vp, i, i, i, d, vp, i, i, vp, i, i, d, vp, i, i]),
@@ -261,6 +262,10 @@ class Context:
         out = (C.c_int * 5)()
         self._check(lib().kot_autotune(self.h, l, out))
         return tuple(out)
+
+    def wait_probe(self, polls: int) -> int:
+        """Run the bounded-wait failure probe; returns its status (ERR_TIMEOUT expected)."""
+        return lib().kot_wait_probe(self.h, polls)
 
     def profile_every(self, every: int):
         return self._check(lib().kot_profile_every(self.h, every))

@@ -356,6 +356,65 @@ def test_potentials_reproduce_the_solved_estimator():
     assert e.value.status == kot.ERR_STATE
 
 
+@pytest.mark.parametrize("l", [1, 2, 3, 5, 17, 33, 129])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tiny_and_odd_sizes(l, precision):
+    # odd sizes against every tile edge (32-wide FP64 tiles, 64-wide K tiles, 128-row MMA tiles,
+    # clusters of one CTA): features, the residual map, and a short solve whose reported residual
+    # the oracle reproduces at the returned iterate
+    p = wl.paper_regime(seed=40 + l, d=2, n=30, l=l)
+    F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
+    ctx = kot.Context(device=0, precision=precision, max_iter=30)
+    ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
+    z = Z(l)
+    ctx.get_features(None, None, None, z, None, None, None, None, None)
+    np.testing.assert_allclose(N(z), F.z, rtol=1e-13, atol=1e-15)
+    g, X = _point(F, 3, 0.5)
+    ref = ko.residual(F, g, X)
+    norms = Z(3)
+    ctx.residual(T(g), T(X), None, None, None, None, norms)
+    assert N(norms)[2] == pytest.approx(ref.norm, rel=1e-9)
+    gg, XX = Z(l), Z(l, l)
+    res = ctx.ssn_solve(1e-9, gg, XX, allow_no_convergence=True)
+    assert res.status in (kot.OK, kot.ERR_NO_CONVERGENCE)
+    assert res.residual == pytest.approx(ko.residual(F, N(gg), N(XX)).norm, rel=1e-6, abs=1e-13)
+
+
+def test_nonfinite_start_is_reported():
+    p = WORKLOADS["paper_d2_l50"]()
+    F, ctx = _features(p)
+    g0 = np.zeros(p.l)
+    g0[3] = np.nan
+    g = Z(p.l)
+    with pytest.raises(kot.KotError) as e:
+        ctx.ssn_solve(p.tol, g, None, T(g0))
+    assert e.value.status == kot.ERR_NONFINITE
+    res = ctx.ssn_solve(p.tol, g)                 # the context stays usable
+    assert res.status == kot.OK
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_resume_from_a_checkpoint(precision):
+    # checkpoint/resume is a warm start: stop after a few iterations, hand (gamma, X) back in, and
+    # the resumed solve reaches the tolerance at the same optimum as an uninterrupted one
+    p = WORKLOADS["paper_d2_l50"]()
+    F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
+    ctx = kot.Context(device=0, precision=precision, max_iter=3)
+    ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
+    g, X = Z(p.l), Z(p.l, p.l)
+    r1 = ctx.ssn_solve(p.tol, g, X, allow_no_convergence=True)
+    assert r1.status == kot.ERR_NO_CONVERGENCE and r1.iters == 3
+    ckpt_g, ckpt_X = g.clone(), X.clone()
+    c2 = kot.Context(device=0, precision=precision)
+    c2.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
+    g2, X2 = Z(p.l), Z(p.l, p.l)
+    r2 = c2.ssn_solve(p.tol, g2, X2, ckpt_g, ckpt_X)
+    assert r2.status == kot.OK
+    assert ko.residual(F, N(g2), N(X2)).norm <= p.tol * (1 + 1e-6)
+    fstar, _ = _optimum(F)
+    assert r2.objective == pytest.approx(fstar, rel=1e-6)
+
+
 def test_error_paths():
     ctx = kot.Context(device=0)
     g = Z(4)

@@ -189,3 +189,17 @@ def test_autotune_records_valid_choices():
     with pytest.raises(kot.KotError) as e:
         ctx.autotune(0)
     assert e.value.status == kot.ERR_INVALID
+
+
+def test_bounded_wait_gives_up_with_a_status():
+    # failure detection without a fault: a kernel waits on an mbarrier nothing completes, with the
+    # bounded poll of the tensor-core pipelines; it gives up (here after ~10^5 polls), the call
+    # returns KOT_ERR_TIMEOUT, and the context keeps working
+    ctx = kot.Context(device=0)
+    assert ctx.wait_probe(100000) == kot.ERR_TIMEOUT
+    assert "probe" in ctx.last_error()
+    x = torch.ones((8, 8), dtype=torch.float64, device=DEV)
+    c = torch.zeros((8, 8), dtype=torch.float64, device=DEV)
+    ctx.dense_product(8, 8, 8, 1.0, x, 8, 0, x, 8, 0, 0.0, c, 8, pieces=-6)
+    assert torch.all(c == 8.0)
+    assert ctx.wait_probe(0) == kot.ERR_INVALID
