@@ -28,7 +28,7 @@ from paper_2310_14087_gb300 import workloads  # noqa: E402
 
 METRIC = "SSN solves/s to ||R||<=1e-6 (time-to-residual = ms_per_step), FP64 vs mixed"
 WORKLOADS = {
-    # BASELINE shapes in the Sec. 5 parameter regime (sigma^2 = 0.005, lambda1 = 1/l,
+    # The timed shapes (d, n, l) in the Sec. 5 parameter regime (sigma^2 = 0.005, lambda1 = 1/l,
     # lambda2 = 1/sqrt(n), unit-cube filling points).  Step k of rank r solves the problem drawn
     # with seed 100 * (r + 1) + k: Algorithm 2's iteration count varies strongly with rounding
     # (the trajectories of two correct runs separate near the solution), so the metric is taken

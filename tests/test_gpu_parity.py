@@ -521,7 +521,7 @@ def test_mixed_solve_full_size_bench_workload():
 
 
 def test_mixed_residual_sample_at_l1024():
-    # BASELINE's large-l shape (d = 10, n = 2000, l = 1024, Sec. 5 regime): the emulated-FP64
+    # the large-l shape (d = 10, n = 2000, l = 1024, Sec. 5 regime): the emulated-FP64
     # residual map against the oracle's at one point
     p = wl.paper_regime(seed=3, d=10, n=2000, l=1024)
     F, _ = _features(p)
