@@ -254,8 +254,8 @@ kot_status kot_autotune(kot_ctx* ctx, int l, int* choice);
 
 /* ---- tracing: per-kernel-class launch statistics (not part of the paper's method) ----
  * Kernel classes: 0 FP64 GEMM tiles, 1 Jacobi eigensolver (FP64, one launch per
- * decomposition), 2 Jacobi eigensolver (FP32), 3 kernel mean
- * embeddings, 4 embedding-norm pair sums, 5 Gram matrices Q and K, 6 Cholesky diagonal block,
+ * decomposition), 2 reserved (unused), 3 kernel mean embeddings and potentials,
+ * 4 embedding-norm pair sums, 5 Gram matrices Q and K, 6 Cholesky diagonal block,
  * 7 tensor-core (tcgen05) GEMM tiles, 8 eigenbasis refinement correction, 9 FP64-emulating
  * tensor-core GEMM (k_oz_gemm), 10 its slicing and finalize kernels.
  * kot_profile(ctx, mask) turns on timing of the classes whose bit is set in mask (0 = off) and

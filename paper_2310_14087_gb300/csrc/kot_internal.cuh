@@ -40,15 +40,16 @@ long long launch_total();
 enum KClass : int {
   KC_GEMM_F64 = 0,      // k_gemm_f64
   KC_JACOBI = 1,        // k_jacobi_coop (all sweeps of one decomposition, FP64)
-  KC_JACOBI_F32 = 2,    // k_jacobi_coop<float> (mixed precision)
-  KC_EMBED = 3,         // k_embed
+  KC_RESERVED_2 = 2,    // unused (kept so that the class numbers of kot.h stay stable)
+  KC_EMBED = 3,         // k_embed, k_potential (kernel sums over samples)
   KC_PAIRS = 4,         // k_pair_tiles
   KC_GRAM = 5,          // k_gram
   KC_CHOL = 6,          // Cholesky diagonal / panel kernels
   KC_GEMM_TC = 7,       // k_tc_gemm_bf16 (tcgen05 tensor-core GEMM)
-  KC_REFINE = 8,        // k_refine_correction (eigenbasis refinement step; its GEMMs are gemm_f64)
+  KC_REFINE = 8,        // k_refine_correction (eigenbasis refinement step; its products are
+                        // counted as gemm_f64 or gemm_oz)
   KC_GEMM_OZ = 9,       // k_oz_gemm (FP64-accurate products emulated on the tensor cores)
-  KC_OZ_AUX = 10,       // k_oz_rowexp + k_oz_split + k_oz_finalize (slicing and FP64 result)
+  KC_OZ_AUX = 10,       // slicing (k_oz_split_cluster, or k_oz_rowexp + k_oz_split) and k_oz_finalize
   KC_COUNT = 11
 };
 

@@ -63,7 +63,7 @@ EXPORTS = ["kot_default_options", "kot_create", "kot_destroy", "kot_last_error",
            "kot_embedding_sqnorm_noalloc", "kot_dense_product", "kot_get_trace", "kot_eig_sym",
            "kot_eg_solve", "kot_potentials", "kot_profile_every", "kot_autotune", "kot_wait_probe"]
 
-KERNEL_CLASSES = ["gemm_f64", "jacobi_f64", "jacobi_f32", "embed", "pair_sums", "gram",
+KERNEL_CLASSES = ["gemm_f64", "jacobi_f64", "reserved", "embed", "pair_sums", "gram",
                   "cholesky", "gemm_tc", "eig_refine", "gemm_oz", "oz_aux"]
 
 
