@@ -307,6 +307,8 @@ __global__ void __launch_bounds__(32 * SK_WARPS, 1) k_gemm_f64_sk(SkArgs a) {
 // (coalesced across i), partial sums reduced through shared memory.
 __global__ void __launch_bounds__(1024) k_coldot_upper(int l, const double* __restrict__ R,
                                                        const double* __restrict__ Y, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double part[32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int i = blockIdx.x * 32 + tx;
@@ -331,6 +333,8 @@ __global__ void __launch_bounds__(1024) k_coldot_upper(int l, const double* __re
 
 __global__ void k_gemv(int n, double alpha, const double* __restrict__ A,
                        const double* __restrict__ x, double beta, double* __restrict__ y) {
+  pdl_wait();
+  pdl_trigger();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= n) return;
   const double* row = A + (size_t)warp * n;
@@ -356,6 +360,8 @@ __device__ double block_sum(double v, double* sh) {
 
 __global__ void k_dot_partial(size_t n, const double* __restrict__ x, const double* __restrict__ y,
                               double* __restrict__ partial) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[256];
   double acc = 0.0;
   for (size_t i = blockIdx.x * 256 + threadIdx.x; i < n; i += (size_t)gridDim.x * 256)
@@ -365,6 +371,8 @@ __global__ void k_dot_partial(size_t n, const double* __restrict__ x, const doub
 }
 
 __global__ void k_sum_partials(int nb, const double* __restrict__ partial, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[256];
   double acc = 0.0;
   for (int i = threadIdx.x; i < nb; i += 256) acc += partial[i];
@@ -376,6 +384,8 @@ __global__ void k_sum_partials(int nb, const double* __restrict__ partial, doubl
 // *out = sum_i x_i y_i (y null: sum x_i^2), fixed summation order.
 __global__ void __launch_bounds__(1024) k_dot_one(size_t n, const double* __restrict__ x,
                                                   const double* __restrict__ y, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[1024];
   double acc = 0.0;
   for (size_t i = threadIdx.x; i < n; i += 1024) acc = fma(x[i], y ? y[i] : x[i], acc);
@@ -390,6 +400,8 @@ __global__ void __launch_bounds__(1024) k_dot_one(size_t n, const double* __rest
 __global__ void __launch_bounds__(1024) k_cg_step(int n, const double* __restrict__ Hp, double* __restrict__ p,
                                                   double* __restrict__ x, double* __restrict__ e,
                                                   double* __restrict__ sc, int cur) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[1024];
   const int t = threadIdx.x;
   double acc = 0.0;
@@ -423,6 +435,8 @@ __global__ void __launch_bounds__(1024) k_cg_step(int n, const double* __restric
 // One block writes out directly; several blocks write partial pairs that k_sum_pairs adds.
 __global__ void k_two_norms(size_t n1, const double* __restrict__ x, size_t n2, const double* __restrict__ a,
                             const double* __restrict__ b, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[256];
   double s1 = 0.0, s2 = 0.0;
   const size_t stride = (size_t)gridDim.x * 256;
@@ -441,6 +455,8 @@ __global__ void k_two_norms(size_t n1, const double* __restrict__ x, size_t n2, 
 }
 
 __global__ void k_sum_pairs(int nb, const double* __restrict__ partial, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[256];
   double s1 = 0.0, s2 = 0.0;
   for (int i = threadIdx.x; i < nb; i += 256) {
@@ -459,6 +475,8 @@ __global__ void k_sum_pairs(int nb, const double* __restrict__ partial, double* 
 // y = alpha A x + mu x + v  (A: n x n row-major; v may be null)
 __global__ void k_hmatvec(int n, double alpha, const double* __restrict__ A, const double* __restrict__ x,
                           double mu, const double* __restrict__ v, double* __restrict__ y) {
+  pdl_wait();
+  pdl_trigger();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= n) return;
   const double* row = A + (size_t)warp * n;
@@ -475,6 +493,8 @@ __global__ void k_hmatvec(int n, double alpha, const double* __restrict__ A, con
 
 __global__ void k_axpby(size_t n, double a, const double* __restrict__ x, double b,
                         const double* __restrict__ y, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
     double v = a * x[i];
@@ -488,6 +508,8 @@ __global__ void k_axpby(size_t n, double a, const double* __restrict__ x, double
 __global__ void k_axpy_ratio(size_t n, const double* __restrict__ num, const double* __restrict__ den,
                              double sgn, const double* __restrict__ x, double* __restrict__ y,
                              double* __restrict__ flag) {
+  pdl_wait();
+  pdl_trigger();
   const double dn = *den;
   if (!(dn > 0.0)) {
     if (flag && blockIdx.x == 0 && threadIdx.x == 0) *flag = 1.0;
@@ -501,18 +523,24 @@ __global__ void k_axpy_ratio(size_t n, const double* __restrict__ num, const dou
 // y = x + (num / den) y with the ratio read from device memory
 __global__ void k_xpby_ratio(size_t n, const double* __restrict__ x, const double* __restrict__ num,
                              const double* __restrict__ den, double* __restrict__ y) {
+  pdl_wait();
+  pdl_trigger();
   const double b = *num / *den;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     y[i] = fma(b, y[i], x[i]);
 }
 
 __global__ void k_fill(size_t n, double v, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)
     out[i] = v;
 }
 
 __global__ void k_symmetrize(int l, double* A) {
+  pdl_wait();
+  pdl_trigger();
   const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
   if (i < l && j < l && i < j) {
     double v = 0.5 * (A[(size_t)i * l + j] + A[(size_t)j * l + i]);
@@ -522,18 +550,24 @@ __global__ void k_symmetrize(int l, double* A) {
 }
 
 __global__ void k_add_diag(int l, double v, double* A, int lda) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < l) A[(size_t)i * lda + i] += v;
 }
 
 __global__ void k_copy_mat(int rows, int cols, const double* __restrict__ A, int lda,
                            double* __restrict__ B, int ldb) {
+  pdl_wait();
+  pdl_trigger();
   const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
   if (i < rows && j < cols) B[(size_t)i * ldb + j] = A[(size_t)i * lda + j];
 }
 
 __global__ void k_sym_sum(int l, const double* __restrict__ G, const double* __restrict__ S,
                           double inv_mu, int complement, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
   if (i >= l || j >= l) return;
   double g = G[(size_t)i * l + j] + G[(size_t)j * l + i];
@@ -649,13 +683,13 @@ void gemm_f64(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alp
 }
 
 void coldot_upper(cudaStream_t st, int l, const double* R, const double* Y, double* out) {
-  k_coldot_upper<<<cdiv(l, 32), dim3(32, 32), 0, st>>>(l, R, Y, out);
+  launch_pdl(k_coldot_upper, dim3(cdiv(l, 32)), dim3(32, 32), 0, st, l, R, Y, out);
   KOT_CHECK_LAUNCH();
 }
 
 void gemv_f64(cudaStream_t st, int n, double alpha, const double* A, const double* x,
               double beta, double* y) {
-  k_gemv<<<cdiv((size_t)n * 32, 256), 256, 0, st>>>(n, alpha, A, x, beta, y);
+  launch_pdl(k_gemv, dim3(cdiv((size_t)n * 32, 256)), dim3(256), 0, st, n, alpha, A, x, beta, y);
   KOT_CHECK_LAUNCH();
 }
 
@@ -665,28 +699,28 @@ constexpr size_t kOneBlockN = 1u << 14;
 void dot_f64(cudaStream_t st, int n, const double* x, const double* y, double* out,
              double* partial) {
   if ((size_t)n <= kOneBlockN) {
-    k_dot_one<<<1, 1024, 0, st>>>((size_t)n, x, y, out);
+    launch_pdl(k_dot_one, dim3(1), dim3(1024), 0, st, (size_t)n, x, y, out);
     KOT_CHECK_LAUNCH();
     return;
   }
-  k_dot_partial<<<kReduceBlocks, 256, 0, st>>>((size_t)n, x, y, partial);
-  k_sum_partials<<<1, 256, 0, st>>>(kReduceBlocks, partial, out);
+  launch_pdl(k_dot_partial, dim3(kReduceBlocks), dim3(256), 0, st, (size_t)n, x, y, partial);
+  launch_pdl(k_sum_partials, dim3(1), dim3(256), 0, st, kReduceBlocks, partial, out);
   KOT_LAUNCHED(2);
 }
 
 void sumsq_f64(cudaStream_t st, size_t n, const double* x, double* out, double* partial) {
   if (n <= kOneBlockN) {
-    k_dot_one<<<1, 1024, 0, st>>>(n, x, nullptr, out);
+    launch_pdl(k_dot_one, dim3(1), dim3(1024), 0, st, n, x, nullptr, out);
     KOT_CHECK_LAUNCH();
     return;
   }
-  k_dot_partial<<<kReduceBlocks, 256, 0, st>>>(n, x, nullptr, partial);
-  k_sum_partials<<<1, 256, 0, st>>>(kReduceBlocks, partial, out);
+  launch_pdl(k_dot_partial, dim3(kReduceBlocks), dim3(256), 0, st, n, x, nullptr, partial);
+  launch_pdl(k_sum_partials, dim3(1), dim3(256), 0, st, kReduceBlocks, partial, out);
   KOT_LAUNCHED(2);
 }
 
 void cg_step(cudaStream_t st, int n, const double* Hp, double* p, double* x, double* e, double* sc, int cur) {
-  k_cg_step<<<1, 1024, 0, st>>>(n, Hp, p, x, e, sc, cur);
+  launch_pdl(k_cg_step, dim3(1), dim3(1024), 0, st, n, Hp, p, x, e, sc, cur);
   KOT_CHECK_LAUNCH();
 }
 
@@ -694,64 +728,64 @@ void two_norms(cudaStream_t st, size_t n1, const double* x, size_t n2, const dou
                double* out2, double* partial) {
   const size_t n = std::max(n1, n2);
   if (n <= kOneBlockN / 4) {
-    k_two_norms<<<1, 256, 0, st>>>(n1, x, n2, a, b, out2);
+    launch_pdl(k_two_norms, dim3(1), dim3(256), 0, st, n1, x, n2, a, b, out2);
     KOT_CHECK_LAUNCH();
     return;
   }
   const int nb = kReduceBlocks / 2;   // partial holds kReduceBlocks doubles: nb pairs
-  k_two_norms<<<nb, 256, 0, st>>>(n1, x, n2, a, b, partial);
-  k_sum_pairs<<<1, 256, 0, st>>>(nb, partial, out2);
+  launch_pdl(k_two_norms, dim3(nb), dim3(256), 0, st, n1, x, n2, a, b, partial);
+  launch_pdl(k_sum_pairs, dim3(1), dim3(256), 0, st, nb, partial, out2);
   KOT_LAUNCHED(2);
 }
 
 void hmatvec(cudaStream_t st, int n, double alpha, const double* A, const double* x, double mu,
              const double* v, double* y) {
-  k_hmatvec<<<cdiv((size_t)n * 32, 256), 256, 0, st>>>(n, alpha, A, x, mu, v, y);
+  launch_pdl(k_hmatvec, dim3(cdiv((size_t)n * 32, 256)), dim3(256), 0, st, n, alpha, A, x, mu, v, y);
   KOT_CHECK_LAUNCH();
 }
 
 void axpby(cudaStream_t st, size_t n, double a, const double* x, double b, const double* y,
            double* out) {
-  k_axpby<<<std::min(cdiv(n, 256), 1216), 256, 0, st>>>(n, a, x, b, y, out);
+  launch_pdl(k_axpby, dim3(std::min(cdiv(n, 256), 1216)), dim3(256), 0, st, n, a, x, b, y, out);
   KOT_CHECK_LAUNCH();
 }
 
 void axpy_ratio(cudaStream_t st, size_t n, const double* num, const double* den, double sgn,
                 const double* x, double* y, double* flag) {
-  k_axpy_ratio<<<std::min(cdiv(n, 256), 1216), 256, 0, st>>>(n, num, den, sgn, x, y, flag);
+  launch_pdl(k_axpy_ratio, dim3(std::min(cdiv(n, 256), 1216)), dim3(256), 0, st, n, num, den, sgn, x, y, flag);
   KOT_CHECK_LAUNCH();
 }
 
 void xpby_ratio(cudaStream_t st, size_t n, const double* x, const double* num, const double* den,
                 double* y) {
-  k_xpby_ratio<<<std::min(cdiv(n, 256), 1216), 256, 0, st>>>(n, x, num, den, y);
+  launch_pdl(k_xpby_ratio, dim3(std::min(cdiv(n, 256), 1216)), dim3(256), 0, st, n, x, num, den, y);
   KOT_CHECK_LAUNCH();
 }
 
 void fill(cudaStream_t st, size_t n, double v, double* out) {
-  k_fill<<<std::min(cdiv(n, 256), 1216), 256, 0, st>>>(n, v, out);
+  launch_pdl(k_fill, dim3(std::min(cdiv(n, 256), 1216)), dim3(256), 0, st, n, v, out);
   KOT_CHECK_LAUNCH();
 }
 
 void symmetrize(cudaStream_t st, int l, double* A) {
-  k_symmetrize<<<dim3(cdiv(l, 32), cdiv(l, 8)), dim3(32, 8), 0, st>>>(l, A);
+  launch_pdl(k_symmetrize, dim3(cdiv(l, 32), cdiv(l, 8)), dim3(32, 8), 0, st, l, A);
   KOT_CHECK_LAUNCH();
 }
 
 void add_diag(cudaStream_t st, int l, double v, double* A, int lda) {
-  k_add_diag<<<cdiv(l, 256), 256, 0, st>>>(l, v, A, lda);
+  launch_pdl(k_add_diag, dim3(cdiv(l, 256)), dim3(256), 0, st, l, v, A, lda);
   KOT_CHECK_LAUNCH();
 }
 
 void copy_mat(cudaStream_t st, int rows, int cols, const double* A, int lda, double* B, int ldb) {
   if (rows <= 0 || cols <= 0) return;
-  k_copy_mat<<<dim3(cdiv(cols, 32), cdiv(rows, 8)), dim3(32, 8), 0, st>>>(rows, cols, A, lda, B, ldb);
+  launch_pdl(k_copy_mat, dim3(cdiv(cols, 32), cdiv(rows, 8)), dim3(32, 8), 0, st, rows, cols, A, lda, B, ldb);
   KOT_CHECK_LAUNCH();
 }
 
 void sym_sum(cudaStream_t st, int l, const double* G, const double* S, double inv_mu,
              int complement, double* out) {
-  k_sym_sum<<<dim3(cdiv(l, 32), cdiv(l, 8)), dim3(32, 8), 0, st>>>(l, G, S, inv_mu, complement, out);
+  launch_pdl(k_sym_sum, dim3(cdiv(l, 32), cdiv(l, 8)), dim3(32, 8), 0, st, l, G, S, inv_mu, complement, out);
   KOT_CHECK_LAUNCH();
 }
 

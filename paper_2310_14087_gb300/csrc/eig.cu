@@ -115,6 +115,8 @@ __global__ void k_gather(int l, int lp, const double* __restrict__ A, const doub
 __global__ void k_refine_correction(int l, int ld, const double* __restrict__ S, const double* __restrict__ G,
                                     double* __restrict__ F, double* __restrict__ lam,
                                     unsigned long long* __restrict__ mx) {
+  pdl_wait();
+  pdl_trigger();
   const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
   // lam_k = S_kk / G_kk for the block's 32 columns and 8 rows, one division each
   __shared__ double lcol[32], lrow[8];
@@ -534,7 +536,7 @@ int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
     KOT_CUDA(cudaMemsetAsync(w.mx.p, 0, 2 * sizeof(unsigned long long), st));
     {
       ProfScope ps(st, KC_REFINE, 12.0 * (double)L2, 8.0 * 3.0 * (double)L2);
-      k_refine_correction<<<g2, b2, 0, st>>>(l, lds, S, G, w.F.p, w.lam.p, w.mx.p);
+      launch_pdl(k_refine_correction, dim3(g2), dim3(b2), 0, st, l, lds, S, G, w.F.p, w.lam.p, w.mx.p);
       KOT_CHECK_LAUNCH();
       KOT_LAUNCHED(1);
     }

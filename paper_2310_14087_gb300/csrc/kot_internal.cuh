@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/kot.h"
@@ -34,6 +35,33 @@ long long launch_total();
     KOT_CUDA(cudaPeekAtLastError());      \
   } while (0)
 #define KOT_CHECK_LAUNCH() KOT_LAUNCHED(1)
+
+// ------------------------------------------------------------------ programmatic dependent launch
+// A kernel launched by launch_pdl may be scheduled while its predecessor in the stream is still
+// running (programmatic stream serialisation, sm_90 and later).  Such a kernel calls pdl_wait()
+// before its first global-memory access and before any early exit: the wait returns once every
+// prerequisite grid has completed with its writes visible, and a grid that cannot complete
+// before its own wait returned keeps completion ordered along the stream.  pdl_trigger() after
+// the wait lets the successor's CTAs be scheduled onto free SMs while this grid runs.  Both
+// instructions are no-ops in a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  KOT_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
 
 // ------------------------------------------------------------------ launch profiler
 // Kernel classes the profiler can time (kot_kernel_class in kot.h uses the same numbering).

@@ -20,6 +20,8 @@ __device__ __forceinline__ double xi_of(double si, double sj, double mu) {
 // is scaled by 1/(2 mu), column j in alpha by 1/mu - xi(sig_j, sig_r).
 __global__ void k_t_weights(int rows, int l, int nb, const double* __restrict__ sig, double mu,
                             int complement, double* __restrict__ V) {
+  pdl_wait();
+  pdl_trigger();
   const int j = blockIdx.x * 32 + threadIdx.x, r = blockIdx.y * 8 + threadIdx.y;
   if (r >= rows || j >= l) return;
   double w;
@@ -34,6 +36,8 @@ __global__ void k_t_weights(int rows, int l, int nb, const double* __restrict__ 
 }
 
 __global__ void k_count_nonpos(int l, const double* __restrict__ sig, int* __restrict__ nb) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ int sh[256];
   int c = 0;
   for (int i = threadIdx.x; i < l; i += 256) c += (sig[i] <= 0.0);
@@ -52,12 +56,12 @@ void t_weights(cudaStream_t st, int l, int nb, const double* sig, double mu, int
                double* V) {
   const int rows = complement ? nb : l - nb;
   if (rows <= 0) return;
-  k_t_weights<<<dim3(cdiv(l, 32), cdiv(rows, 8)), dim3(32, 8), 0, st>>>(rows, l, nb, sig, mu, complement, V);
+  launch_pdl(k_t_weights, dim3(cdiv(l, 32), cdiv(rows, 8)), dim3(32, 8), 0, st, rows, l, nb, sig, mu, complement, V);
   KOT_CHECK_LAUNCH();
 }
 
 void count_nonpos(cudaStream_t st, int l, const double* sig, int* nb) {
-  k_count_nonpos<<<1, 256, 0, st>>>(l, sig, nb);
+  launch_pdl(k_count_nonpos, dim3(1), dim3(256), 0, st, l, sig, nb);
   KOT_CHECK_LAUNCH();
 }
 

@@ -181,6 +181,9 @@ __global__ void __launch_bounds__(OzCfg<BN>::THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
+  // barrier set-up and the tensor-memory allocation above overlap the slicing kernel's tail
+  pdl_wait();
+  pdl_trigger();
 
   if (warp == EPI) {
     if (lane == 0) {
@@ -451,6 +454,8 @@ __global__ void k_oz_split(OzSplitArgs a) {
 template <int KW>
 __global__ void __launch_bounds__(32 * kSplitRows) k_oz_split_cluster(OzSplitArgs a) {
   constexpr int COLS = 64 * KW;
+  pdl_wait();
+  pdl_trigger();
   cg::cluster_group cluster = cg::this_cluster();
   const OzOperand& o = a.op[blockIdx.z];
   const int r0 = blockIdx.y * 32, k0 = blockIdx.x * COLS;
@@ -535,13 +540,15 @@ void launch_split_cluster(cudaStream_t st, const OzSplitArgs& sa, int Kp, int rb
   cfg.blockDim = dim3(32, kSplitRows);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attrs[1];
+  cudaLaunchAttribute attrs[2];
   attrs[0].id = cudaLaunchAttributeClusterDimension;
   attrs[0].val.clusterDim.x = (unsigned)ncta;
   attrs[0].val.clusterDim.y = 1;
   attrs[0].val.clusterDim.z = 1;
+  attrs[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // see launch_pdl
+  attrs[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attrs;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   KOT_CUDA(cudaLaunchKernelEx(&cfg, k_oz_split_cluster<KW>, sa));
 }
 
@@ -564,6 +571,8 @@ __device__ __forceinline__ double oz_value(const float2* __restrict__ W, size_t 
 __global__ void k_oz_finalize(int M, int N, int splits, const float2* __restrict__ W,
                               const double* __restrict__ fa, const double* __restrict__ fb, double beta,
                               double* __restrict__ C, int ldc, int sym) {
+  pdl_wait();
+  pdl_trigger();
   const size_t MN = (size_t)M * N;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < MN;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -594,7 +603,8 @@ void launch_oz_gemm(cudaStream_t st, const CUtensorMap& ta, const CUtensorMap& t
     KOT_CUDA(cudaFuncSetAttribute(k_oz_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
     attr_set[dev] = true;
   }
-  k_oz_gemm<BN><<<dim3(cdiv(N, BN), cdiv(M, OZ_BM), splits), Cfg::THREADS, Cfg::SMEM, st>>>(ta, tb, P);
+  launch_pdl(k_oz_gemm<BN>, dim3(cdiv(N, BN), cdiv(M, OZ_BM), splits), dim3(Cfg::THREADS), Cfg::SMEM, st, ta, tb,
+             P);
 }
 }  // namespace
 
@@ -725,7 +735,8 @@ void gemm_oz(cudaStream_t st, OzWork& w, int M, int N, int K, const TcOperand& A
   const int fgrid = (int)std::min<size_t>(cdiv(MN, 256), (size_t)nsm * 8);
   {
     ProfScope ps(st, KC_OZ_AUX, 0.0, 8.0 * splits * (double)MN + 8.0 * (beta == 0.0 ? 1.0 : 2.0) * (double)MN);
-    k_oz_finalize<<<fgrid, 256, 0, st>>>(M, N, splits, w.w.p, w.fac.p, w.fac.p + M, beta, C, ldc, sym ? 1 : 0);
+    launch_pdl(k_oz_finalize, dim3(fgrid), dim3(256), 0, st, M, N, splits, (const float2*)w.w.p,
+               (const double*)w.fac.p, (const double*)(w.fac.p + M), beta, C, ldc, sym ? 1 : 0);
     KOT_LAUNCHED(1);
   }
 }
