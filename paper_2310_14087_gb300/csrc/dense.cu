@@ -331,6 +331,34 @@ __global__ void __launch_bounds__(1024) k_coldot_upper(int l, const double* __re
   }
 }
 
+// One 32 x 32 block per 32 columns: lane tx owns column i, row group ty strides the rows.
+__global__ void __launch_bounds__(1024) k_coldot_rows(int rows, int n, const double* __restrict__ A, int lda,
+                                                      const double* __restrict__ Y, int ldy, double scale,
+                                                      double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ double part[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * 32 + tx;
+  double acc0 = 0.0, acc1 = 0.0;
+  if (i < n) {
+    int a = ty;
+    for (; a + 32 < rows; a += 64) {
+      acc0 = fma(A[(size_t)a * lda + i], Y[(size_t)a * ldy + i], acc0);
+      acc1 = fma(A[(size_t)(a + 32) * lda + i], Y[(size_t)(a + 32) * ldy + i], acc1);
+    }
+    if (a < rows) acc0 = fma(A[(size_t)a * lda + i], Y[(size_t)a * ldy + i], acc0);
+  }
+  part[ty][tx] = acc0 + acc1;
+  __syncthreads();
+  if (ty == 0 && i < n) {
+    double s = 0.0;
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) s += part[r][tx];
+    out[i] = scale * s;
+  }
+}
+
 __global__ void k_gemv(int n, double alpha, const double* __restrict__ A,
                        const double* __restrict__ x, double beta, double* __restrict__ y) {
   pdl_wait();
@@ -445,6 +473,33 @@ __global__ void k_two_norms(size_t n1, const double* __restrict__ x, size_t n2, 
     const double d = a[i] - b[i];
     s2 = fma(d, d, s2);
   }
+  s1 = block_sum<256>(s1, sh);
+  __syncthreads();
+  s2 = block_sum<256>(s2, sh);
+  if (threadIdx.x == 0) {
+    out[2 * blockIdx.x] = s1;
+    out[2 * blockIdx.x + 1] = s2;
+  }
+}
+
+__global__ void k_eig_norms(size_t n1, const double* __restrict__ x, int rows, int cols, int ld, int nb,
+                            const double* __restrict__ A, const double* __restrict__ W,
+                            const double* __restrict__ base, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ double sh[256];
+  double s1 = 0.0, s2 = 0.0;
+  const size_t stride = (size_t)gridDim.x * 256;
+  for (size_t i = blockIdx.x * 256 + threadIdx.x; i < n1; i += stride) s1 = fma(x[i], x[i], s1);
+  const size_t n2 = (size_t)rows * cols;
+  for (size_t i = blockIdx.x * 256 + threadIdx.x; i < n2; i += stride) {
+    const int r = (int)(i / cols), j = (int)(i - (size_t)r * cols);
+    const size_t o = (size_t)r * ld + j;
+    const bool bar = j < nb;
+    const double d = A[o] - (W ? (bar ? 1.0 : 2.0) * W[o] : 0.0);
+    s2 = fma(bar ? 2.0 * d : d, d, s2);
+  }
+  if (base && blockIdx.x == 0 && threadIdx.x == 0) s2 += *base;
   s1 = block_sum<256>(s1, sh);
   __syncthreads();
   s2 = block_sum<256>(s2, sh);
@@ -575,6 +630,8 @@ __global__ void k_sym_sum(int l, const double* __restrict__ G, const double* __r
 }
 
 inline int cdiv(size_t a, int b) { return (int)((a + b - 1) / b); }
+// grid of the elementwise helpers: at least one block, so that n = 0 is a valid (empty) launch
+inline int elementwise_grid(size_t n) { return std::max(1, std::min(cdiv(n, 256), 1216)); }
 
 }  // namespace
 
@@ -687,6 +744,14 @@ void coldot_upper(cudaStream_t st, int l, const double* R, const double* Y, doub
   KOT_CHECK_LAUNCH();
 }
 
+void coldot_rows(cudaStream_t st, int rows, int n, const double* A, int lda, const double* Y, int ldy,
+                 double scale, double* out) {
+  if (n <= 0) return;
+  launch_pdl(k_coldot_rows, dim3(cdiv(n, 32)), dim3(32, 32), 0, st, std::max(rows, 0), n, A, lda, Y, ldy, scale,
+             out);
+  KOT_CHECK_LAUNCH();
+}
+
 void gemv_f64(cudaStream_t st, int n, double alpha, const double* A, const double* x,
               double beta, double* y) {
   launch_pdl(k_gemv, dim3(cdiv((size_t)n * 32, 256)), dim3(256), 0, st, n, alpha, A, x, beta, y);
@@ -738,6 +803,21 @@ void two_norms(cudaStream_t st, size_t n1, const double* x, size_t n2, const dou
   KOT_LAUNCHED(2);
 }
 
+void eig_norms(cudaStream_t st, size_t n1, const double* x, int rows, int cols, int ld, int nb,
+               const double* A, const double* W, const double* base, double* out2, double* partial) {
+  const size_t n = std::max(n1, (size_t)std::max(rows, 0) * std::max(cols, 0));
+  if (rows <= 0 || cols <= 0) rows = cols = 0;
+  if (n <= kOneBlockN / 4) {
+    launch_pdl(k_eig_norms, dim3(1), dim3(256), 0, st, n1, x, rows, cols, ld, nb, A, W, base, out2);
+    KOT_CHECK_LAUNCH();
+    return;
+  }
+  const int nbk = kReduceBlocks / 2;   // partial holds kReduceBlocks doubles: nbk pairs
+  launch_pdl(k_eig_norms, dim3(nbk), dim3(256), 0, st, n1, x, rows, cols, ld, nb, A, W, base, partial);
+  launch_pdl(k_sum_pairs, dim3(1), dim3(256), 0, st, nbk, partial, out2);
+  KOT_LAUNCHED(2);
+}
+
 void hmatvec(cudaStream_t st, int n, double alpha, const double* A, const double* x, double mu,
              const double* v, double* y) {
   launch_pdl(k_hmatvec, dim3(cdiv((size_t)n * 32, 256)), dim3(256), 0, st, n, alpha, A, x, mu, v, y);
@@ -746,24 +826,24 @@ void hmatvec(cudaStream_t st, int n, double alpha, const double* A, const double
 
 void axpby(cudaStream_t st, size_t n, double a, const double* x, double b, const double* y,
            double* out) {
-  launch_pdl(k_axpby, dim3(std::min(cdiv(n, 256), 1216)), dim3(256), 0, st, n, a, x, b, y, out);
+  launch_pdl(k_axpby, dim3(elementwise_grid(n)), dim3(256), 0, st, n, a, x, b, y, out);
   KOT_CHECK_LAUNCH();
 }
 
 void axpy_ratio(cudaStream_t st, size_t n, const double* num, const double* den, double sgn,
                 const double* x, double* y, double* flag) {
-  launch_pdl(k_axpy_ratio, dim3(std::min(cdiv(n, 256), 1216)), dim3(256), 0, st, n, num, den, sgn, x, y, flag);
+  launch_pdl(k_axpy_ratio, dim3(elementwise_grid(n)), dim3(256), 0, st, n, num, den, sgn, x, y, flag);
   KOT_CHECK_LAUNCH();
 }
 
 void xpby_ratio(cudaStream_t st, size_t n, const double* x, const double* num, const double* den,
                 double* y) {
-  launch_pdl(k_xpby_ratio, dim3(std::min(cdiv(n, 256), 1216)), dim3(256), 0, st, n, x, num, den, y);
+  launch_pdl(k_xpby_ratio, dim3(elementwise_grid(n)), dim3(256), 0, st, n, x, num, den, y);
   KOT_CHECK_LAUNCH();
 }
 
 void fill(cudaStream_t st, size_t n, double v, double* out) {
-  launch_pdl(k_fill, dim3(std::min(cdiv(n, 256), 1216)), dim3(256), 0, st, n, v, out);
+  launch_pdl(k_fill, dim3(elementwise_grid(n)), dim3(256), 0, st, n, v, out);
   KOT_CHECK_LAUNCH();
 }
 

@@ -79,6 +79,7 @@ struct kot_ctx {
   ResState rw, rv, rt;
   EigSlot ew, ev, et, e1, e2;
   DevBuf<double> M1, M2, M3, M4, M5, M6, TU, TV, TW, TG;
+  DevBuf<double> Cb, A2, Wx;   // eigenbasis CG: P^T R, P^T at2 P, alpha rows of P^T T[Phi*(x)] P
   DevBuf<double> v1, v2, v3, v4, v5, v6, w1, w2, w3;
   DevBuf<double> Fvg, FvX;     // F(v) of the EG iterate, from its last residual evaluation
   bool fv_valid = false;
@@ -143,7 +144,8 @@ void ensure(kot_ctx* C, int l) {
   const size_t L2 = (size_t)l * l, L = (size_t)l;
   for (DevBuf<double>* b : {&C->Q, &C->K, &C->R, &C->X, &C->vX, &C->tX, &C->dX, &C->M1, &C->M2,
                             &C->M3, &C->M4, &C->M5, &C->M6, &C->TU, &C->TV, &C->TW, &C->TG,
-                            &C->rw.r2, &C->rv.r2, &C->rt.r2, &C->FvX, &C->Plast})
+                            &C->Cb, &C->A2, &C->Wx, &C->rw.r2, &C->rv.r2, &C->rt.r2, &C->FvX,
+                            &C->Plast})
     b->alloc(L2);
   C->Fvg.alloc(L);
   for (DevBuf<double>* b : {&C->z, &C->w_mu, &C->w_nu, &C->c, &C->g, &C->vg, &C->tg, &C->dg,
@@ -366,6 +368,42 @@ void t_apply(kot_ctx* C, const EigSlot& e, double mu, const double* S, double* o
   sym_sum(C->st, l, C->TG.p, S, 1.0 / mu, comp ? 1 : 0, out);
 }
 
+// The Schur operator of Algorithm 1 in the eigenbasis of Z = P diag(sig) P^T.  With Cb = P^T R
+// (row j: eigen-index j, column i: point i), P^T Phi*(p) P = Cb diag(p) Cb^T, so
+// T[Phi*(p)] = P (Psi o Cb diag(p) Cb^T) P^T and Phi(T[Phi*(p)]) = diag(Cb^T (Psi o ...) Cb).  Psi
+// (Sec. 4.3) is symmetric and vanishes on alpha-bar x alpha-bar, so its alpha rows determine the
+// product: with W = the alpha rows of Psi o Cb diag(p) Cb^T, the alpha x alpha block halved (the
+// weights of the G + G^T form), T[Phi*(p)] = G + G^T for G = P_alpha W P^T and
+// Phi(T[Phi*(p)]) = 2 diag(Cb_alpha^T W Cb).  That is two |alpha| x l x l products per operator
+// application, against 2 l^3 + 4 min(|alpha|, |alpha-bar|) l^2 multiply-adds for
+// phi_star / T / phi.  Products run at the phase's precision (three slices inside tensor-core CG).
+// Out: W (|alpha| x l, ld l), Hp = Q p/(2 lambda2) + mu p + Phi(T[Phi*(p)]); Y: |alpha| x l scratch.
+void cg_gemm(kot_ctx* C, bool ta, bool tb, int M, int N, int K, const double* A, const double* B,
+             const double* s, double* out) {
+  const int l = C->l;
+  if (mixed(C))
+    gemm_oz(C->st, C->oz, M, N, K, TcOperand{A, l, ta, s}, TcOperand{B, l, !tb, nullptr}, kCgSlices, 1.0, 0.0,
+            out, l, false);
+  else
+    gemm_acc(C->st, ozp(C), ta, tb, M, N, K, 1.0, A, l, B, l, s, 0.0, out, l, 0);
+}
+
+void schur_eig(kot_ctx* C, const EigSlot& e, double mu, const double* p, double* W, double* Y, double* Hp) {
+  const int l = C->l, nb = e.nb, na = l - nb;
+  cudaStream_t st = C->st;
+  const double* Cb = C->Cb.p;
+  const double* Ca = Cb + (size_t)nb * l;
+  if (na == 0) {
+    fill(st, l, 0.0, C->v5.p);
+  } else {
+    cg_gemm(C, false, true, na, l, l, Ca, Cb, p, W);     // W = Cb_alpha diag(p) Cb^T
+    t_weights(st, l, nb, e.sig.p, mu, 0, W);
+    cg_gemm(C, false, false, na, l, l, W, Cb, nullptr, Y);   // Y = W Cb
+    coldot_rows(st, na, l, Ca, l, Y, l, 2.0, C->v5.p);
+  }
+  hmatvec(st, l, 1.0 / (2.0 * C->lambda2), C->Q.p, p, mu, C->v5.p, Hp);
+}
+
 // Symmetric QMR (Freund and Nachtigal, no preconditioner) on H x = a1 from the x in dgam, whose
 // residual a1 - H x is in ev and T[Phi*(x)] in TPx.  The Lanczos residual rl drives the
 // recurrences; x moves along the smoothed direction d, and the true residual and T[Phi*(x)]
@@ -475,18 +513,38 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
   axpby(st, l, -1.0, r.r1.p, -1.0 / (mu + 1.0), C->v1.p, a1);
   axpby(st, L2, -1.0 / (mu + 1.0), rT, 0.0, nullptr, at2);
   C->force64 = !allow_tc;
+  // CG works on the eigenbasis form of the operator (see schur_eig); symmetric QMR keeps the
+  // direct form phi_star / T / phi.  Set-up, once per direction with FP64-accuracy products:
+  // Cb = P^T R, and for the stopping test A2 = P^T at2 P with |A2 on alpha-bar x alpha-bar|^2.
+  const bool eigcg = C->opt.schur_solver != 1;
+  const int nb = e.nb, na = l - nb;
+  double* sc = C->scal.p;
+  double* Wx = C->Wx.p;
+  if (eigcg) {
+    gemm_acc(st, ozp(C), true, false, l, l, l, 1.0, e.P.p, l, C->R.p, l, nullptr, 0.0, C->Cb.p, l, G_KHI_COL);
+    if (cg_tol_abs <= 0) {
+      gemm_acc(st, ozp(C), true, false, l, l, l, 1.0, e.P.p, l, at2, l, nullptr, 0.0, C->TU.p, l, 0);
+      gemm_acc(st, ozp(C), false, false, l, l, l, 1.0, C->TU.p, l, e.P.p, l, nullptr, 0.0, C->A2.p, l, 0);
+      eig_norms(st, 0, nullptr, nb, nb, l, 0, C->A2.p, nullptr, nullptr, sc + 10, C->partial.p);
+    }
+  }
   for (int phase = 0; phase < (refine ? 2 : 1); ++phase) {
     if (phase == 1) C->force64 = true;   // always verify a tensor-core direction in FP64
     if (phase == 0) {
       fill(st, l, 0.0, dgam);
-      fill(st, L2, 0.0, TPx);
+      if (eigcg) fill(st, (size_t)na * l, 0.0, Wx);
+      else fill(st, L2, 0.0, TPx);
       KOT_CUDA(cudaMemcpyAsync(ev, a1, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
     } else {
       // e = a1 - H x with FP64 products, and T[Phi*(x)] recomputed alongside
-      phi_star_nd(C, dgam, C->M5.p);
-      t_apply(C, e, mu, C->M5.p, TPx);
-      phi_nd(C, TPx, C->v5.p, C->M5.p);
-      hmatvec(st, l, 1.0 / (2.0 * C->lambda2), C->Q.p, dgam, mu, C->v5.p, Hp);
+      if (eigcg) {
+        schur_eig(C, e, mu, dgam, Wx, C->M6.p, Hp);
+      } else {
+        phi_star_nd(C, dgam, C->M5.p);
+        t_apply(C, e, mu, C->M5.p, TPx);
+        phi_nd(C, TPx, C->v5.p, C->M5.p);
+        hmatvec(st, l, 1.0 / (2.0 * C->lambda2), C->Q.p, dgam, mu, C->v5.p, Hp);
+      }
       axpby(st, l, 1.0, a1, -1.0, Hp, ev);
     }
     KOT_CUDA(cudaMemcpyAsync(pv, ev, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -496,14 +554,15 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
     } else {
       // CG with its step lengths kept on the device: ||e||^2 alternates between scal[5] and
       // scal[6], p^T H p is scal[3], scal[7] flags a non-positive curvature; the host reads the
-      // norms of the stopping test (and the flag) once per iteration
-      double* sc = C->scal.p;
+      // norms of the stopping test (and the flag) once per iteration.  T[Phi*(x)] is carried as
+      // the alpha rows Wx of its eigenbasis form, and ||at2 - T[Phi*(x)]||_F is measured there.
       int cur = 0;
       fill(st, 1, 0.0, sc + 7);
       sumsq_f64(st, l, ev, sc + 5, C->partial.p);
       while (true) {
         // stop test at the current iterate: ||e|| vs tau min(1, kappa ||r|| ||dw||)
-        two_norms(st, l, dgam, L2, at2, TPx, sc + 1, C->partial.p);
+        if (cg_tol_abs > 0) sumsq_f64(st, l, dgam, sc + 1, C->partial.p);
+        else eig_norms(st, l, dgam, na, l, l, nb, C->A2.p + (size_t)nb * l, Wx, sc + 11, sc + 1, C->partial.p);
         fetch(C, 8);
         const double ee = C->hs[5 + cur];
         const double enorm = std::sqrt(ee);
@@ -514,7 +573,7 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
         bool stop;
         if (cg_tol_abs > 0) stop = enorm <= cg_tol_abs;
         else {
-          const double dw = std::sqrt(C->hs[1]) + std::sqrt(C->hs[2]);
+          const double dw = std::sqrt(C->hs[1]) + std::sqrt(std::max(C->hs[2], 0.0));
           stop = enorm <= C->opt.tau * std::min(1.0, C->opt.kappa * r.norm * dw);
         }
         met = stop;
@@ -523,15 +582,12 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
           break;
         }
         if (stop || it >= cap) break;
-        // Hp = Q p/(2 lambda2) + mu p + Phi(T[Phi*(p)])
-        phi_star_nd(C, pv, C->M5.p);
-        t_apply(C, e, mu, C->M5.p, C->M6.p);
-        phi_nd(C, C->M6.p, C->v5.p, C->M5.p);
-        hmatvec(st, l, 1.0 / (2.0 * C->lambda2), C->Q.p, pv, mu, C->v5.p, Hp);
+        // Hp = Q p/(2 lambda2) + mu p + Phi(T[Phi*(p)]); M5 = alpha rows of T[Phi*(p)] (eigenbasis)
+        schur_eig(C, e, mu, pv, C->M5.p, C->M6.p, Hp);
         // a = ||e||^2 / p^T H p: x += a p, e -= a H p, p = e + b p (one block, scalars on the
         // device), then T[Phi*(x)] += a T[Phi*(p)]
         cg_step(st, l, Hp, pv, dgam, ev, sc, cur);
-        axpy_ratio(st, L2, sc + 5 + cur, sc + 3, 1.0, C->M6.p, TPx, nullptr);
+        axpy_ratio(st, (size_t)na * l, sc + 5 + cur, sc + 3, 1.0, C->M5.p, Wx, nullptr);
         cur ^= 1;
         ++it;
       }
@@ -542,6 +598,16 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
   // 1: tensor-core direction accepted by the FP64 check as is; 2: FP64 steps were added
   C->last_dir_kind = refine ? (refined_steps == 0 ? 1 : 2) : 0;
   C->force64 = false;
+  // T[Phi*(x)] = G + G^T with G = P_alpha Wx P^T (FP64-accuracy products)
+  if (eigcg) {
+    if (na == 0) {
+      fill(st, L2, 0.0, TPx);
+    } else {
+      gemm_acc(st, ozp(C), false, true, na, l, l, 1.0, Wx, l, e.P.p, l, nullptr, 0.0, C->TW.p, l, 0);
+      gemm_acc(st, ozp(C), false, false, l, l, na, 1.0, e.P.p + nb, l, C->TW.p, l, nullptr, 0.0, C->TG.p, l, 0);
+      sym_sum(st, l, C->TG.p, nullptr, 1.0 / mu, 0, TPx);
+    }
+  }
   axpby(st, L2, 1.0, at2, -1.0, TPx, dX);
   return total;   // a timed-out tensor-core wait is reported when the API call returns (run())
 }
@@ -734,6 +800,7 @@ kot_status kot_destroy(kot_ctx* C) {
   for (DevBuf<double>* b : {&C->Q, &C->K, &C->R, &C->z, &C->w_mu, &C->w_nu, &C->c, &C->g, &C->X,
                             &C->vg, &C->vX, &C->tg, &C->tX, &C->dg, &C->dX, &C->M1, &C->M2,
                             &C->M3, &C->M4, &C->M5, &C->M6, &C->TU, &C->TV, &C->TW, &C->TG,
+                            &C->Cb, &C->A2, &C->Wx,
                             &C->v1, &C->v2, &C->v3, &C->v4, &C->v5, &C->v6, &C->w1, &C->w2,
                             &C->w3, &C->partial,
                             &C->scal, &C->bounds, &C->rw.r1, &C->rw.r2, &C->rv.r1, &C->rv.r2,

@@ -161,6 +161,10 @@ void gemm_f64(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alp
 // out[i] = sum_a R[a,i] * Y[a,i] for a <= i  (Phi(X) = diag(R^T X R) with Y = X R)
 void coldot_upper(cudaStream_t st, int l, const double* R, const double* Y, double* out);
 
+// out[i] = scale * sum_{a < rows} A[a,i] * Y[a,i], i < n (row-major, leading dimensions lda, ldy)
+void coldot_rows(cudaStream_t st, int rows, int n, const double* A, int lda, const double* Y, int ldy,
+                 double scale, double* out);
+
 // y = alpha * A x + beta * y (A: n x n row-major)
 void gemv_f64(cudaStream_t st, int n, double alpha, const double* A, const double* x,
               double beta, double* y);
@@ -177,6 +181,12 @@ void cg_step(cudaStream_t st, int n, const double* Hp, double* p, double* x, dou
 // out2[0] = |x|^2 (n1 entries), out2[1] = |a - b|^2 (n2 entries); partial: kReduceBlocks doubles
 void two_norms(cudaStream_t st, size_t n1, const double* x, size_t n2, const double* a, const double* b,
                double* out2, double* partial);
+// Norms of the CG stopping test in the eigenbasis: out2[0] = |x|^2 (n1 entries) and
+// out2[1] = (base ? *base : 0) + sum_{r < rows, j < cols} w_j (A[r,j] - c_j W[r,j])^2 with
+// (w_j, c_j) = (2, 1) for j < nb and (1, 2) for j >= nb; W may be null (zero).  partial:
+// kReduceBlocks doubles.
+void eig_norms(cudaStream_t st, size_t n1, const double* x, int rows, int cols, int ld, int nb,
+               const double* A, const double* W, const double* base, double* out2, double* partial);
 // y = alpha A x + mu x + v (v may be null)
 void hmatvec(cudaStream_t st, int n, double alpha, const double* A, const double* x, double mu,
              const double* v, double* y);
