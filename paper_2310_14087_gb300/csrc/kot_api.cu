@@ -505,29 +505,35 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
   int total = 0, refined_steps = 0;
   bool met = false;
   // right-hand side: a1 = -r1 - Phi(r2 + T[r2])/(mu+1), at2 = -(r2 + T[r2])/(mu+1), formed
-  // once with FP64-accuracy products (CG iterates, not the system, carry the reduced precision)
-  C->force64 = true;
-  t_apply(C, e, mu, r.r2.p, rT);
-  axpby(st, L2, 1.0, r.r2.p, 1.0, rT, rT);
-  phi_nd(C, rT, C->v1.p, C->M2.p);
-  axpby(st, l, -1.0, r.r1.p, -1.0 / (mu + 1.0), C->v1.p, a1);
-  axpby(st, L2, -1.0 / (mu + 1.0), rT, 0.0, nullptr, at2);
-  C->force64 = !allow_tc;
-  // CG works on the eigenbasis form of the operator (see schur_eig); symmetric QMR keeps the
-  // direct form phi_star / T / phi.  Set-up, once per direction with FP64-accuracy products:
-  // Cb = P^T R, and for the stopping test A2 = P^T at2 P with |A2 on alpha-bar x alpha-bar|^2.
+  // once with FP64-accuracy products (CG iterates, not the system, carry the reduced precision).
+  // CG works on the eigenbasis form of the operator (see schur_eig) and forms the right-hand
+  // side there too: with Cb = P^T R and B = P^T r2 P, A2 = P^T at2 P = -(1 + Psi) o B/(mu + 1)
+  // and Phi(at2) = diag(Cb^T A2 Cb), so a1 = -r1 + diag(Cb^T A2 Cb); the stopping test reads A2
+  // (and |A2 on alpha-bar x alpha-bar|^2), and the direction ends as dX = P (A2 - P^T T[Phi*(x)] P) P^T.
+  // Symmetric QMR keeps the direct form phi_star / T / phi.
   const bool eigcg = C->opt.schur_solver != 1;
   const int nb = e.nb, na = l - nb;
   double* sc = C->scal.p;
   double* Wx = C->Wx.p;
   if (eigcg) {
-    gemm_acc(st, ozp(C), true, false, l, l, l, 1.0, e.P.p, l, C->R.p, l, nullptr, 0.0, C->Cb.p, l, G_KHI_COL);
-    if (cg_tol_abs <= 0) {
-      gemm_acc(st, ozp(C), true, false, l, l, l, 1.0, e.P.p, l, at2, l, nullptr, 0.0, C->TU.p, l, 0);
-      gemm_acc(st, ozp(C), false, false, l, l, l, 1.0, C->TU.p, l, e.P.p, l, nullptr, 0.0, C->A2.p, l, 0);
-      eig_norms(st, 0, nullptr, nb, nb, l, 0, C->A2.p, nullptr, nullptr, sc + 10, C->partial.p);
-    }
+    OzWork* oz = ozp(C);
+    gemm_acc(st, oz, true, false, l, l, l, 1.0, e.P.p, l, C->R.p, l, nullptr, 0.0, C->Cb.p, l, G_KHI_COL);
+    gemm_acc(st, oz, true, false, l, l, l, 1.0, e.P.p, l, r.r2.p, l, nullptr, 0.0, C->TU.p, l, 0);
+    gemm_acc(st, oz, false, false, l, l, l, 1.0, C->TU.p, l, e.P.p, l, nullptr, 0.0, C->TV.p, l, G_SYM);
+    rhs_weights(st, l, nb, e.sig.p, mu, C->TV.p, C->A2.p);
+    gemm_acc(st, oz, false, false, l, l, l, 1.0, C->A2.p, l, C->Cb.p, l, nullptr, 0.0, C->TW.p, l, 0);
+    coldot_rows(st, l, l, C->Cb.p, l, C->TW.p, l, 1.0, C->v1.p);
+    axpby(st, l, -1.0, r.r1.p, 1.0, C->v1.p, a1);
+    if (cg_tol_abs <= 0) eig_norms(st, 0, nullptr, nb, nb, l, 0, C->A2.p, nullptr, nullptr, sc + 10, C->partial.p);
+  } else {
+    C->force64 = true;
+    t_apply(C, e, mu, r.r2.p, rT);
+    axpby(st, L2, 1.0, r.r2.p, 1.0, rT, rT);
+    phi_nd(C, rT, C->v1.p, C->M2.p);
+    axpby(st, l, -1.0, r.r1.p, -1.0 / (mu + 1.0), C->v1.p, a1);
+    axpby(st, L2, -1.0 / (mu + 1.0), rT, 0.0, nullptr, at2);
   }
+  C->force64 = !allow_tc;
   for (int phase = 0; phase < (refine ? 2 : 1); ++phase) {
     if (phase == 1) C->force64 = true;   // always verify a tensor-core direction in FP64
     if (phase == 0) {
@@ -598,17 +604,14 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
   // 1: tensor-core direction accepted by the FP64 check as is; 2: FP64 steps were added
   C->last_dir_kind = refine ? (refined_steps == 0 ? 1 : 2) : 0;
   C->force64 = false;
-  // T[Phi*(x)] = G + G^T with G = P_alpha Wx P^T (FP64-accuracy products)
   if (eigcg) {
-    if (na == 0) {
-      fill(st, L2, 0.0, TPx);
-    } else {
-      gemm_acc(st, ozp(C), false, true, na, l, l, 1.0, Wx, l, e.P.p, l, nullptr, 0.0, C->TW.p, l, 0);
-      gemm_acc(st, ozp(C), false, false, l, l, na, 1.0, e.P.p + nb, l, C->TW.p, l, nullptr, 0.0, C->TG.p, l, 0);
-      sym_sum(st, l, C->TG.p, nullptr, 1.0 / mu, 0, TPx);
-    }
+    // dX = at2 - T[Phi*(x)] = P D P^T, D = A2 - P^T T[Phi*(x)] P (FP64-accuracy products)
+    assemble_dir(st, l, nb, C->A2.p, Wx, C->TG.p);
+    gemm_acc(st, ozp(C), false, true, l, l, l, 1.0, C->TG.p, l, e.P.p, l, nullptr, 0.0, C->TW.p, l, 0);
+    gemm_acc(st, ozp(C), false, false, l, l, l, 1.0, e.P.p, l, C->TW.p, l, nullptr, 0.0, dX, l, G_SYM);
+  } else {
+    axpby(st, L2, 1.0, at2, -1.0, TPx, dX);
   }
-  axpby(st, L2, 1.0, at2, -1.0, TPx, dX);
   return total;   // a timed-out tensor-core wait is reported when the API call returns (run())
 }
 

@@ -347,6 +347,11 @@ void gemm_acc(cudaStream_t st, OzWork* oz, bool ta, bool tb, int M, int N, int K
 // alpha-bar by xi (or the complement weights).  See t_apply in kot_api.cu.
 void t_weights(cudaStream_t st, int l, int nb, const double* sig, double mu, int complement,
                double* V);
+// Right-hand side of Algorithm 1 in the eigenbasis: A2 = -(1 + Psi) o B/(mu + 1) for B = P^T r2 P
+// (l x l), i.e. A2 = P^T at2 P.
+void rhs_weights(cudaStream_t st, int l, int nb, const double* sig, double mu, const double* B, double* A2);
+// D = A2 - P^T T[Phi*(x)] P with T[Phi*(x)] given by its alpha rows Wx (alpha x alpha halved).
+void assemble_dir(cudaStream_t st, int l, int nb, const double* A2, const double* Wx, double* D);
 // Count of eigenvalues <= 0 in sorted sig (device) -> *nb (device int)
 void count_nonpos(cudaStream_t st, int l, const double* sig, int* nb);
 
