@@ -45,9 +45,16 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12     # SMs x FP64 FMA/clk x 2 flop
 ROOF_CLASS = {"mixed": "gemm_oz", "fp64": "gemm_f64"}
 PROFILE_EVERY = 8   # events around one launch in 8 of that class (less perturbation of the step)
 # DRAM bytes (read + write) of one k_oz_gemm launch of this workload's shape (300 x 300 x 300,
-# six slices) from an ncu capture (profiles/oz_gemm_emulated_fp64_l300_l1024_l2048.md); the
-# algorithmic bytes of that launch (the sliced operands) are 2 x 300 x 6 x 320 x 2 = 2.30 MB
-ROOF_TRAFFIC = {("gemm_oz", "paper_d5_n1000_l300"): 2340096.0}
+# six slices) from ncu captures of the current kernel; the algorithmic bytes of that launch (the
+# sliced operands) are 2 x 300 x 6 x 320 x 2 = 2.30 MB.  Empty: the kernel gained its
+# programmatic-launch wait/trigger after the last capture (2.34 MB,
+# profiles/oz_gemm_emulated_fp64_l300_l1024_l2048.md), which is reported beside the null
+# "traffic" as traffic_last_capture.
+ROOF_TRAFFIC = {}
+ROOF_TRAFFIC_LAST = {("gemm_oz", "paper_d5_n1000_l300"): {
+    "bytes": 2340096.0,
+    "note": "ncu dram__bytes_read+write of one 300x300x300 six-slice launch, taken before the "
+            "kernel's griddepcontrol wait/trigger was added"}}
 
 
 def seed_of(rank: int, step: int) -> int:
@@ -478,6 +485,7 @@ def report(args, probs, world, ms_max, ms_local, stats, launches, iters, conv, c
                     "unit": unit, "frac": achieved / peak, "traffic": traffic,
                     "traffic_note": None if traffic is None else
                     "ncu dram__bytes_read+write of one 300x300x300 six-slice launch (bytes)",
+                    "traffic_last_capture": ROOF_TRAFFIC_LAST.get((dom, args.workload)),
                     "launches_timed": s.launches, "timed_one_in": PROFILE_EVERY if args.profile == "roofline" else 1,
                     "avg_launch_us": per_launch_ms * 1e3,
                     "share_of_step": s.ms * (PROFILE_EVERY if args.profile == "roofline" else 1) / ms_local,

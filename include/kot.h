@@ -17,6 +17,12 @@
  * No entry point aborts the process, and no kernel waits without an iteration bound.
  *
  * Threads: a context is used by one host thread at a time.
+ *
+ * Launches: kernels that follow one another on the context's stream are launched with
+ * programmatic stream serialisation (each waits for its predecessor's completion inside the
+ * kernel, after its own set-up), so set-up overlaps the previous kernel's tail.  Setting the
+ * environment variable KOT_PDL=0 before the first call gives plain stream-ordered launches of
+ * the same kernels (same arithmetic, same results).
  */
 #ifndef KOT_H
 #define KOT_H

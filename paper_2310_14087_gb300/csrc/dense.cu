@@ -5,6 +5,7 @@
 // bound by the FP64 pipe: the design goal is to keep all 152 SMs busy (small 32 x 32 tiles) and
 // to skip work the triangular Cholesky factor makes zero, not to stage operands for tensor cores.
 #include <algorithm>
+#include <cstdlib>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -634,6 +635,14 @@ inline int cdiv(size_t a, int b) { return (int)((a + b - 1) / b); }
 inline int elementwise_grid(size_t n) { return std::max(1, std::min(cdiv(n, 256), 1216)); }
 
 }  // namespace
+
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("KOT_PDL");
+    return !(v && v[0] == '0' && v[1] == '\0');
+  }();
+  return on;
+}
 
 namespace {
 

@@ -548,7 +548,7 @@ void launch_split_cluster(cudaStream_t st, const OzSplitArgs& sa, int Kp, int rb
   attrs[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // see launch_pdl
   attrs[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attrs;
-  cfg.numAttrs = 2;
+  cfg.numAttrs = pdl_enabled() ? 2 : 1;
   KOT_CUDA(cudaLaunchKernelEx(&cfg, k_oz_split_cluster<KW>, sa));
 }
 
