@@ -154,7 +154,10 @@ kot_status kot_residual(kot_ctx* ctx, const double* gamma, const double* X, doub
 
 /* Regularised Newton direction of Eq. (4.2)-(4.3) by Algorithm 1 at w = (gamma, X) with
  * regularisation mu > 0: CG on (Q/(2 lambda2) + mu I + Phi T Phi*) dgamma = a1 with the
- * operator T_k of Sec. 4.3 (G + G^T form when |alpha| <= l/2, complement form otherwise).
+ * operator T_k of Sec. 4.3.  CG applies Phi T Phi* in the eigenbasis of Z (Cb = P^T R formed once
+ * per direction; the alpha rows of Psi o Cb diag(p) Cb^T with the G + G^T weights) and forms a1
+ * and dX there too; schur_solver = 1 applies T directly (G + G^T form when |alpha| <= l/2,
+ * complement form otherwise).  Both are T_k in exact arithmetic.
  * cg_tol_abs > 0 stops CG at ||residual||_2 <= cg_tol_abs (at most 10 l + 50 iterations);
  * cg_tol_abs <= 0 uses the inexact test of Eq. (4.3) with the context's tau, kappa and
  * cg_max_iter.  Outputs: dgamma (l), dX (l x l), cg_iters (host int, may be NULL). */
