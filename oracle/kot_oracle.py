@@ -23,7 +23,11 @@ Readings of points the paper leaves open (each is also an option here):
   * tau = 0.1, kappa = 1 for the inexact-Newton test (Eq. (4.3));
   * theta_0 = 1, theta_min = 1e-6, theta_max = 1e6; alpha1, alpha2, beta0..2 from Sec. 5;
   * ||dw||^2 in the theta rule = (||dgamma||_2 + ||dX||_F)^2 (the norm below Eq. (4.3));
-  * w_0 = v_0 = (0, 0); the EG sequence v is never reset to w.
+  * w_0 = v_0 = (0, 0); the EG sequence v is never reset to w;
+  * R is printed on R^l x R^{l x l}, but the projection onto S^l_+ (symmetric PSD matrices)
+    of a general matrix is that of its symmetric part, so the generalized Jacobian M(Z) of
+    Sec. 4.2, and with it T_k of Sec. 4.3, acts on the symmetric part of its argument.  (Applied
+    to the raw argument, rounding-level asymmetry of X grows by about 1/mu per Newton step.)
 
 Functions whose result is pinned only by properties (no closed form or printed value) say so
 in their docstring.
@@ -276,8 +280,11 @@ def psi_matrix(sig: np.ndarray, mu: float) -> np.ndarray:
 
 
 def t_apply(e: Eig, Psi: np.ndarray, S: np.ndarray) -> np.ndarray:
-    """T_k[S] = P (Psi o (P^T S P)) P^T (Sec. 4.3), the operator form of T_k = P~ L_k P~^T."""
-    return e.P @ (Psi * (e.P.T @ S @ e.P)) @ e.P.T
+    """T_k[S] = P (Psi o (P^T sym(S) P)) P^T (Sec. 4.3), the operator form of T_k = P~ L_k P~^T.
+
+    sym(S): M(Z) is the generalized Jacobian of the projection onto S^l_+, which sees only the
+    symmetric part of a matrix (see the module docstring)."""
+    return e.P @ (Psi * (e.P.T @ sym(S) @ e.P)) @ e.P.T
 
 
 # ----------------------------------------------------------------------------------------
