@@ -577,3 +577,41 @@ def test_mixed_solve_gates(name):
     fstar, gstar = _optimum(F)
     assert res.objective == pytest.approx(fstar, rel=1e-6)
     assert np.abs(N(g) - gstar).max() <= 1e-5 * np.abs(gstar).max()
+
+
+# The five problems bench.py times (Sec. 5 regime, d = 5, n = 1000, l = 300, seeds 100..104).
+# With T acting on the symmetric part of its argument the oracle's runs are insensitive to
+# rounding (perturbing Q and z by up to 1e-7, or T's output by 1e-13, leaves its iteration
+# counts unchanged), so a correct implementation takes about as many iterations.
+BENCH_SEEDS = (100, 101, 102, 103, 104)
+
+
+def _bench_problem(seed):
+    p = wl.paper_regime(seed=seed, d=5, n=1000, l=300)
+    F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
+    return p, F
+
+
+def test_mixed_solve_iterations_track_the_oracle_on_the_bench_problems():
+    ctx = kot.Context(device=0, precision=kot.MIXED)
+    for seed in BENCH_SEEDS:
+        p, F = _bench_problem(seed)
+        ref = ko.ssn_solve(F, p.tol)
+        ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
+        g, X = Z(p.l), Z(p.l, p.l)
+        res = ctx.ssn_solve(p.tol, g, X)
+        assert res.status == kot.OK and ref.converged, seed
+        assert abs(res.iters - ref.iters) <= 3, (seed, res.iters, ref.iters)
+        assert ko.residual(F, N(g), N(X)).norm <= p.tol * (1 + 1e-5), seed
+
+
+@pytest.mark.xfail(strict=False, reason="open: the FP64 form has run to the 200-iteration cap on "
+                   "this problem, where the oracle and the mixed form take 28 iterations")
+def test_fp64_solve_converges_on_bench_seed_102():
+    p, F = _bench_problem(102)
+    ctx = kot.Context(device=0, precision=kot.FP64)
+    ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
+    g, X = Z(p.l), Z(p.l, p.l)
+    res = ctx.ssn_solve(p.tol, g, X, allow_no_convergence=True)
+    assert res.status == kot.OK
+    assert res.iters <= 60
