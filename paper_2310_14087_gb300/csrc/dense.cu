@@ -756,8 +756,8 @@ void coldot_upper(cudaStream_t st, int l, const double* R, const double* Y, doub
 void coldot_rows(cudaStream_t st, int rows, int n, const double* A, int lda, const double* Y, int ldy,
                  double scale, double* out) {
   if (n <= 0) return;
-  launch_pdl(k_coldot_rows, dim3(cdiv(n, 32)), dim3(32, 32), 0, st, std::max(rows, 0), n, A, lda, Y, ldy, scale,
-             out);
+  launch_pdl(k_coldot_rows, dim3(cdiv(n, 32)), dim3(32, 32), 0, st, std::max(rows, 0), n, A, lda, Y, ldy,
+             scale, out);
   KOT_CHECK_LAUNCH();
 }
 

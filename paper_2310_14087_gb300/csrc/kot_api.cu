@@ -524,7 +524,8 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
     gemm_acc(st, oz, false, false, l, l, l, 1.0, C->A2.p, l, C->Cb.p, l, nullptr, 0.0, C->TW.p, l, 0);
     coldot_rows(st, l, l, C->Cb.p, l, C->TW.p, l, 1.0, C->v1.p);
     axpby(st, l, -1.0, r.r1.p, 1.0, C->v1.p, a1);
-    if (cg_tol_abs <= 0) eig_norms(st, 0, nullptr, nb, nb, l, 0, C->A2.p, nullptr, nullptr, sc + 10, C->partial.p);
+    if (cg_tol_abs <= 0)
+      eig_norms(st, 0, nullptr, nb, nb, l, 0, C->A2.p, nullptr, nullptr, sc + 10, C->partial.p);
   } else {
     C->force64 = true;
     t_apply(C, e, mu, r.r2.p, rT);

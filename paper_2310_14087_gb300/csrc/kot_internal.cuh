@@ -45,7 +45,9 @@ long long launch_total();
 // the wait lets the successor's CTAs be scheduled onto free SMs while this grid runs.  Both
 // instructions are no-ops in a kernel launched without the attribute.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 // Programmatic launches are on unless the environment sets KOT_PDL=0 (read once per process),
 // e.g. for a profiler run that should see the plain stream-ordered launches.

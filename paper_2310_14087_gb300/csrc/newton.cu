@@ -90,7 +90,8 @@ void t_weights(cudaStream_t st, int l, int nb, const double* sig, double mu, int
                double* V) {
   const int rows = complement ? nb : l - nb;
   if (rows <= 0) return;
-  launch_pdl(k_t_weights, dim3(cdiv(l, 32), cdiv(rows, 8)), dim3(32, 8), 0, st, rows, l, nb, sig, mu, complement, V);
+  launch_pdl(k_t_weights, dim3(cdiv(l, 32), cdiv(rows, 8)), dim3(32, 8), 0, st, rows, l, nb, sig, mu,
+             complement, V);
   KOT_CHECK_LAUNCH();
 }
 

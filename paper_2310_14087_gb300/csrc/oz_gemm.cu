@@ -603,8 +603,8 @@ void launch_oz_gemm(cudaStream_t st, const CUtensorMap& ta, const CUtensorMap& t
     KOT_CUDA(cudaFuncSetAttribute(k_oz_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
     attr_set[dev] = true;
   }
-  launch_pdl(k_oz_gemm<BN>, dim3(cdiv(N, BN), cdiv(M, OZ_BM), splits), dim3(Cfg::THREADS), Cfg::SMEM, st, ta, tb,
-             P);
+  launch_pdl(k_oz_gemm<BN>, dim3(cdiv(N, BN), cdiv(M, OZ_BM), splits), dim3(Cfg::THREADS), Cfg::SMEM, st,
+             ta, tb, P);
 }
 }  // namespace
 
