@@ -42,7 +42,8 @@ def _system_residual(F, gamma, X, mu):
     return np.linalg.norm(e1), np.linalg.norm(e2), np.linalg.norm(res.r1), np.linalg.norm(res.r2)
 
 
-@pytest.mark.parametrize("seed,antisym,mu", [(0, 0.0, 1e-1), (4, 0.0, 1e-2), (5, 0.0, 1e-3), (0, 1e-3, 1e-2), (4, 1e-4, 1e-3)])
+@pytest.mark.parametrize("seed,antisym,mu", [(0, 0.0, 1e-1), (4, 0.0, 1e-2), (5, 0.0, 1e-3),
+                                              (0, 1e-3, 1e-2), (4, 1e-4, 1e-3)])
 def test_direction_solves_the_regularised_newton_system(seed, antisym, mu):
     F, gamma, X = _point(seed, antisym)
     e1, e2, n1, n2 = _system_residual(F, gamma, X, mu)

@@ -354,6 +354,30 @@ def test_golden_algorithm_constants():
         assert getattr(o, key) == g[key], key
 
 
+def test_eg_operator_is_the_lagrangian_gradient():
+    # F(gamma, X) = (grad_gamma L, -grad_X L) for the min-max objective L of Eq. (4.1):
+    # L = gamma^T Q gamma/(4 lambda2) - gamma^T z/(2 lambda2) + q^2/(4 lambda2)
+    #     - <X, Phi*(gamma) + lambda1 I>.
+    # Central differences of L along random directions give both blocks of F.
+    rng = np.random.default_rng(12)
+    F = _small_features(l=7)
+
+    def L(g, X):
+        S = (F.R * g[None, :]) @ F.R.T + F.lambda1 * np.eye(F.l)
+        return (g @ F.Q @ g / (4 * F.lambda2) - g @ F.z / (2 * F.lambda2) + F.q2 / (4 * F.lambda2)
+                - np.sum(X * S))
+
+    g, X = _point(F, rng)
+    Fg, FX = ko.eg_operator(F, g, X)
+    h = 1e-6
+    for _ in range(3):
+        dg, dX = rng.standard_normal(F.l), _rand_sym(rng, F.l)
+        dLg = (L(g + h * dg, X) - L(g - h * dg, X)) / (2 * h)
+        dLX = (L(g, X + h * dX) - L(g, X - h * dX)) / (2 * h)
+        assert Fg @ dg == pytest.approx(dLg, rel=1e-7, abs=1e-9)
+        assert -np.sum(FX * dX) == pytest.approx(dLX, rel=1e-7, abs=1e-9)
+
+
 def test_eg_step_size_bounds_operator_norm():
     # eta = 1/L must not exceed 1/||linear part||; compute that norm by dense SVD
     F = _small_features(l=5)
