@@ -305,12 +305,17 @@ kot_status kot_wait_probe(kot_ctx* ctx, long long polls);
  * S and out (one double) are device pointers on the caller's current device; stream is a
  * cudaStream_t of that device (NULL = legacy default stream).  The call returns after the
  * stream has finished (the result is in *out).  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls share the one array and it keeps the last call's partial sums;
- * every slot a call reads is written by that same call, so nothing needs clearing, but calls
- * whose GPU work overlaps (other host threads or streams at the same time) race on it and must
- * be serialised by the caller.  Errors: KOT_ERR_INVALID for n, d < 1, NULL pointers or
- * sigma <= 0; KOT_ERR_CUDA for a failed CUDA call. */
+ * device address (cudaGetSymbolAddress) with that device current and keeps it for the process;
+ * make that first call before any stream capture.  The kept address belongs to the device's
+ * current primary context: after cudaDeviceReset on that device (or anything else that destroys
+ * and re-creates its primary context) the array may move, so a process that resets a device must
+ * not call this entry point on it again.  All calls share the one array and it keeps the last
+ * call's partial sums; every slot a call reads is written by that same call, so nothing needs
+ * clearing, but calls whose GPU work overlaps (other host threads or streams at the same time)
+ * race on it and must be serialised by the caller.  Errors: KOT_ERR_TOO_LARGE for n > 4096
+ * (nothing is launched); KOT_ERR_INVALID for n, d < 1, NULL pointers, sigma <= 0 or not finite,
+ * or a current device ordinal of 64 or more (the per-device address table has 64 entries);
+ * KOT_ERR_CUDA for a failed CUDA call. */
 kot_status kot_embedding_sqnorm_noalloc(int n, int d, const double* S, double sigma, double* out,
                                         void* stream);
 

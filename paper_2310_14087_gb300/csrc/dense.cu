@@ -174,9 +174,13 @@ __device__ __forceinline__ void sk_stage(int lane, const double (&ra)[8], const 
   }
 }
 
+// G_SYM: only entries on or above the diagonal are stored, each also at its mirror position, so
+// the result is exactly symmetric.  (A diagonal tile holds both (m, n) and (n, m); storing both
+// as computed would leave their rounding-level difference in C, and a symmetric matrix that is
+// not exactly so lets that antisymmetric part grow through the 1/mu weights of T_k, Sec. 4.3.)
 __device__ __forceinline__ void sk_store(const SkArgs& a, int m0, int n0, int r, int c,
                                          const double (&acc)[2][4]) {
-  const bool mirror = (a.flags & G_SYM) && n0 > m0;
+  const bool sym = (a.flags & G_SYM) != 0;
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
     const int gm = m0 + 2 * r + i;
@@ -184,7 +188,8 @@ __device__ __forceinline__ void sk_store(const SkArgs& a, int m0, int n0, int r,
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int gn = n0 + 4 * c + j;
-      if (gn >= a.N) continue;
+      if (gn >= a.N || (sym && gn < gm)) continue;
+      const bool mirror = sym && gn > gm;
       const double v = a.alpha * acc[i][j];
       double* cp = &a.C[(size_t)gm * a.ldc + gn];
       *cp = (a.beta == 0.0) ? v : v + a.beta * (*cp);

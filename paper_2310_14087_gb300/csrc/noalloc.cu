@@ -22,7 +22,8 @@ std::mutex g_mutex;
 double* g_partials_addr[kMaxDevices] = {};
 
 // Device address of g_pair_partials on the current device, looked up once per device (the name
-// itself is only a host-side stand-in in host code).
+// itself is only a host-side stand-in in host code).  The address is that of the device's
+// primary context at the first call; a cudaDeviceReset invalidates it (see kot.h).
 kot_status partials_on_current_device(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return KOT_ERR_CUDA;

@@ -200,17 +200,19 @@ def test_solve_matches_oracle_fp64(name, prefix):
 
 def test_solve_full_size_bench_workload():
     # the timed workload (d = 5, n = 1000, l = 300, sigma^2 = 0.005, lambda1 = 1/l,
-    # lambda2 = 1/sqrt(n)) in the launch configuration bench.py uses
+    # lambda2 = 1/sqrt(n)) in the launch configuration bench.py uses, gated at the stated FP64
+    # tolerance: relative 1e-8 on f(gamma) against the oracle's solve to the same final residual
+    # (both run Algorithm 2 along the same trajectory; against a tighter reference solve not even
+    # the oracle's own tol-1e-6 result is within 1e-8, see the iteration-count test below)
     p = wl.paper_regime(seed=1, d=5, n=1000, l=300)
     F, ref, ref_hist, res, g, X, hist = _solve_both(p, p.tol)
-    assert res.status == kot.OK
+    assert res.status == kot.OK and ref.converged
     np.testing.assert_allclose(hist[:8], ref_hist[:8], rtol=1e-8)
     check = ko.residual(F, g, X)
     assert check.norm <= p.tol * (1 + 1e-6)
-    # the optimum is unique in gamma; at ||R|| <= 1e-6 both sides sit within the same
-    # tolerance-sized neighbourhood of it
-    assert res.objective == pytest.approx(ref.objective, rel=1e-4)
-    np.testing.assert_allclose(g, ref.gamma, atol=1e-3 * np.abs(ref.gamma).max())
+    assert res.objective == pytest.approx(ref.objective, rel=1e-8)
+    assert np.abs(g - ref.gamma).max() <= 1e-5 * np.abs(ref.gamma).max()
+    assert np.array_equal(X, X.T)            # X stays exactly symmetric (S^l, Sec. 4.1)
 
 
 def test_fp64_objective_gate():
@@ -502,8 +504,9 @@ def test_mixed_residual_matches_oracle(name, scale):
 
 def test_mixed_solve_full_size_bench_workload():
     # the timed workload (d = 5, n = 1000, l = 300, Sec. 5 regime) in the form and launch
-    # configuration bench.py times: the oracle confirms the stopping test at the returned iterate
-    # and the objective sits within the tolerance-sized neighbourhood of the oracle's
+    # configuration bench.py times, gated at the stated mixed-form tolerances against the
+    # oracle's solve to the same final residual: relative 1e-6 on f(gamma) and 1e-5 on gamma
+    # (max norm relative to max |gamma|); the oracle confirms the stopping test at the iterate
     p = wl.paper_regime(seed=1, d=5, n=1000, l=300)
     F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
     ref = ko.ssn_solve(F, p.tol)
@@ -511,13 +514,14 @@ def test_mixed_solve_full_size_bench_workload():
     ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
     g, X = Z(p.l), Z(p.l, p.l)
     res = ctx.ssn_solve(p.tol, g, X)
-    assert res.status == kot.OK
+    assert res.status == kot.OK and ref.converged
     check = ko.residual(F, N(g), N(X))
     assert check.norm <= p.tol * (1 + 1e-5)
     assert res.residual == pytest.approx(check.norm, rel=1e-4, abs=1e-12)
     assert res.objective == pytest.approx(ko.objective(F, N(g)), rel=1e-12)
-    if ref.converged:
-        assert res.objective == pytest.approx(ref.objective, rel=1e-4)
+    assert res.objective == pytest.approx(ref.objective, rel=1e-6)
+    assert np.abs(N(g) - ref.gamma).max() <= 1e-5 * np.abs(ref.gamma).max()
+    assert torch.equal(X, X.T)
 
 
 def test_mixed_residual_sample_at_l1024():
@@ -579,39 +583,49 @@ def test_mixed_solve_gates(name):
     assert np.abs(N(g) - gstar).max() <= 1e-5 * np.abs(gstar).max()
 
 
-# The five problems bench.py times (Sec. 5 regime, d = 5, n = 1000, l = 300, seeds 100..104).
-# With T acting on the symmetric part of its argument the oracle's runs are insensitive to
-# rounding (perturbing Q and z by up to 1e-7, or T's output by 1e-13, leaves its iteration
-# counts unchanged), so a correct implementation takes about as many iterations.
-BENCH_SEEDS = (100, 101, 102, 103, 104)
+# The problems bench.py times (Sec. 5 regime, d = 5, n = 1000, l = 300, seeds 100..119: one
+# per step of a 20-step run).  With T acting on the symmetric part of its argument the oracle's
+# runs are insensitive to rounding (perturbing Q and z by up to 1e-7, or T's output by 1e-13,
+# leaves its iteration counts unchanged), so a correct implementation takes about as many
+# iterations and stops at the same point: the objective within the stated gate of each form.
+BENCH_SEEDS = tuple(range(100, 120))
+_ORACLE = {}
 
 
 def _bench_problem(seed):
-    p = wl.paper_regime(seed=seed, d=5, n=1000, l=300)
-    F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
-    return p, F
+    if seed not in _ORACLE:
+        p = wl.paper_regime(seed=seed, d=5, n=1000, l=300)
+        F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
+        _ORACLE[seed] = (p, F, ko.ssn_solve(F, p.tol))
+    return _ORACLE[seed]
 
 
-def test_mixed_solve_iterations_track_the_oracle_on_the_bench_problems():
-    ctx = kot.Context(device=0, precision=kot.MIXED)
+@pytest.mark.parametrize("precision,obj_rel", [(kot.FP64, 1e-8), (kot.MIXED, 1e-6)])
+def test_solve_iterations_track_the_oracle_on_the_bench_problems(precision, obj_rel):
+    ctx = kot.Context(device=0, precision=precision)
     for seed in BENCH_SEEDS:
-        p, F = _bench_problem(seed)
-        ref = ko.ssn_solve(F, p.tol)
+        p, F, ref = _bench_problem(seed)
         ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
         g, X = Z(p.l), Z(p.l, p.l)
-        res = ctx.ssn_solve(p.tol, g, X)
-        assert res.status == kot.OK and ref.converged, seed
+        res = ctx.ssn_solve(p.tol, g, X, allow_no_convergence=True)
+        assert res.status == kot.OK and ref.converged, (seed, res.iters, ref.iters)
         assert abs(res.iters - ref.iters) <= 3, (seed, res.iters, ref.iters)
         assert ko.residual(F, N(g), N(X)).norm <= p.tol * (1 + 1e-5), seed
+        assert res.objective == pytest.approx(ref.objective, rel=obj_rel), seed
+        assert torch.equal(X, X.T), seed
 
 
-@pytest.mark.xfail(strict=False, reason="open: the FP64 form has run to the 200-iteration cap on "
-                   "this problem, where the oracle and the mixed form take 28 iterations")
-def test_fp64_solve_converges_on_bench_seed_102():
-    p, F = _bench_problem(102)
-    ctx = kot.Context(device=0, precision=kot.FP64)
+@pytest.mark.parametrize("precision", [kot.FP64, kot.MIXED])
+def test_newton_direction_is_exactly_symmetric(precision):
+    # dX is assembled as P D P^T; both product paths store a symmetric result exactly (the FP64
+    # GEMM mirrors every entry above the diagonal, diagonal tiles included), so a symmetric X
+    # stays symmetric and T_k never sees an antisymmetric part to amplify by 1/mu
+    p = WORKLOADS["paper_d5_l97"]()
+    F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
+    ctx = kot.Context(device=0, precision=precision)
     ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
-    g, X = Z(p.l), Z(p.l, p.l)
-    res = ctx.ssn_solve(p.tol, g, X, allow_no_convergence=True)
-    assert res.status == kot.OK
-    assert res.iters <= 60
+    g, X = _point(F, 3, 0.5)
+    for mu in (1e-1, 1e-4):
+        dg, dX = Z(p.l), Z(p.l, p.l)
+        ctx.newton_direction(T(g), T(X), mu, dg, dX)
+        assert torch.equal(dX, dX.T), mu
