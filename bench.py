@@ -1,7 +1,7 @@
 """Benchmark: SSN solves to ||R(w)|| <= 1e-6 per second on GB300 (features + Algorithm 2 per step).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                [--workload NAME] [--precision fp64|mixed]
+                [--workload NAME] [--precision fp64|mixed] [--method ssn|eg|batch|product|features]
 
 A step is one pass of the whole hot path on one synthetic problem: feature assembly (kernel
 embeddings, Gram matrices, Cholesky) followed by Algorithm 2 until the natural residual is at
@@ -44,17 +44,14 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12     # SMs x FP64 FMA/clk x 2 flop
 # perturb the latency-bound step; the per-class breakdown comes from one extra untimed step)
 ROOF_CLASS = {"mixed": "gemm_oz", "fp64": "gemm_f64"}
 PROFILE_EVERY = 8   # events around one launch in 8 of that class (less perturbation of the step)
-# DRAM bytes (read + write) of one k_oz_gemm launch of this workload's shape (300 x 300 x 300,
-# six slices) from ncu captures of the current kernel; the algorithmic bytes of that launch (the
-# sliced operands) are 2 x 300 x 6 x 320 x 2 = 2.30 MB.  Empty: the kernel gained its
-# programmatic-launch wait/trigger after the last capture (2.34 MB,
-# profiles/oz_gemm_emulated_fp64_l300_l1024_l2048.md), which is reported beside the null
-# "traffic" as traffic_last_capture.
-ROOF_TRAFFIC = {}
-ROOF_TRAFFIC_LAST = {("gemm_oz", "paper_d5_n1000_l300"): {
-    "bytes": 2340096.0,
-    "note": "ncu dram__bytes_read+write of one 300x300x300 six-slice launch, taken before the "
-            "kernel's griddepcontrol wait/trigger was added"}}
+# DRAM bytes (read + write) per launch of the dominant kernel, from an ncu capture of the
+# current kernel on a standalone product of the workload's size (bench.py --method product;
+# profiles/ names the command).  The solve's launches of that kernel mix shapes (l x l x l
+# products and the |alpha-bar|- or |alpha|-row products of CG), so the figure is that of the
+# l x l x l six-slice launch; None until a capture of the current kernel exists.
+# (gemm_oz, 300^3, six slices): 2344704 and 2340352 bytes read, 0 written, in the two captured
+# launches (profiles/oz_gemm_emulated_fp64_l300_l1024_l2048.md); algorithmic 2.30 MB of slices.
+ROOF_TRAFFIC = {("gemm_oz", "paper_d5_n1000_l300", 6): 2342528.0}
 
 
 def seed_of(rank: int, step: int) -> int:
@@ -142,12 +139,33 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def oracle_solve(p):
+def oracle_solve(p, with_features=False):
     from oracle import kot_oracle as ko
     t = time.perf_counter()
     F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
     r = ko.ssn_solve(F, p.tol)
-    return time.perf_counter() - t, r
+    t = time.perf_counter() - t
+    return (t, r, F) if with_features else (t, r)
+
+
+ONE_CORE_ENV = {"OPENBLAS_NUM_THREADS": "1", "OMP_NUM_THREADS": "1", "MKL_NUM_THREADS": "1",
+                "GOTO_NUM_THREADS": "1"}
+
+
+def oracle_one_core(workload: str, step: int = 0):
+    """The oracle's solve of one problem timed in a child process whose BLAS uses one thread
+    (the thread count is fixed when NumPy loads its BLAS, so it takes a fresh interpreter)."""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "t, r = bench.oracle_solve(bench.make_problem(%r, 0, %d)); "
+            "print(json.dumps({'s': t, 'iters': r.iters, 'converged': bool(r.converged)}))"
+            % (ROOT, workload, step))
+    env = dict(os.environ, **ONE_CORE_ENV)
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                             timeout=600)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:   # the baseline is reported, never required
+        return {"error": str(e)[:200]}
 
 
 def run_reference(args, rank, world):
@@ -170,7 +188,8 @@ def run_reference(args, rank, world):
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, **config_of(args.workload), "tol": 1e-6,
-                   "oracle_iters": iters, "converged": conv},
+                   "oracle_iters": iters, "converged": conv,
+                   "one_core": one_core_line(args.workload)},
         "cpu_baseline": {"value": val, "unit": "solves/s", "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} full solves (features + Algorithm 2 to 1e-6, one "
                                    f"problem per step) of {args.workload}, NumPy/LAPACK with "
@@ -178,6 +197,14 @@ def run_reference(args, rank, world):
         "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def one_core_line(workload):
+    r = oracle_one_core(workload)
+    if "s" not in r:
+        return r
+    return {"value": (1.0 if r["converged"] else 0.0) / r["s"], "unit": "solves/s", "cores": 1,
+            "iters": r["iters"], "sample": f"the step-0 problem of {workload}, BLAS on one thread"}
 
 
 def main():
@@ -193,10 +220,17 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true", help="do not time the host-buffer path")
     ap.add_argument("--profile", default="roofline", choices=["roofline", "all", "none"],
                     help="kernel classes timed with CUDA events inside the timed region")
-    ap.add_argument("--method", default="ssn", choices=["ssn", "eg", "batch"],
+    ap.add_argument("--method", default="ssn", choices=["ssn", "eg", "batch", "product", "features", "eig",
+                                                        "bootstrap"],
                     help="ssn: Algorithm 2 (the headline); eg: the pure extragradient method of "
                          "App. F, a fixed number of steps per problem; batch: kot_batch_solve "
-                         "over an uneven batch (d 2..20, n 200..2000, l 32..512)")
+                         "over an uneven batch (d 2..20, n 200..2000, l 32..512); product: one "
+                         "FP64-accurate l x l x l product per step (kot_dense_product, the "
+                         "solve's dominant kernel alone, for ncu); features: the feature "
+                         "assembly alone (kot_build_features); eig: cold symmetric "
+                         "eigendecompositions (kot_eig_sym) per size bucket, --sizes; bootstrap: "
+                         "--batch resamples sharing the filling points (kot_bootstrap_solve) against "
+                         "as many separate feature builds and solves")
     ap.add_argument("--batch", type=int, default=32, help="problems per batch (--method batch)")
     ap.add_argument("--autotune", action="store_true",
                     help="run kot_autotune for l first (untimed); off by default: its standalone "
@@ -205,6 +239,9 @@ def main():
                     help="outer-iteration cap of Algorithm 2 (lower it to time iterations at large l)")
     ap.add_argument("--workers", type=int, default=8, help="concurrent solves (--method batch)")
     ap.add_argument("--eg-steps", type=int, default=200, help="EG steps per problem (--method eg)")
+    ap.add_argument("--slices", type=int, default=6, help="slices of the emulated product (--method product)")
+    ap.add_argument("--sizes", default="64,160,300,512,1024,2048", help="sizes l (--method eig)")
+    ap.add_argument("--gram-fp32", action="store_true", help="Gram matrices in FP32 (--method features)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -225,6 +262,14 @@ def main():
         return eg_bench(args, world, rank, local_rank, dev)
     if args.method == "batch":
         return batch_bench(args, world, rank, local_rank, dev)
+    if args.method == "product":
+        return product_bench(args, world, rank, local_rank, dev)
+    if args.method == "features":
+        return features_bench(args, world, rank, local_rank, dev)
+    if args.method == "eig":
+        return eig_bench(args, world, rank, local_rank, dev)
+    if args.method == "bootstrap":
+        return bootstrap_bench(args, world, rank, local_rank, dev)
     p = make_problem(args.workload, rank, 0)
     tuned = None
     if args.autotune:
@@ -299,6 +344,18 @@ def main():
         o_ms_local, _, _, o_iters, o_conv = timed(other_prec)
         _, o_ms_max, o_value = job_totals(sum(o_conv), o_ms_local, world, dev)
 
+    # ---- untimed: the step-0 problem once more in each form, kept for the errors vs the oracle
+    finals = {}
+    for prec in ([main_prec] + ([] if args.skip_other else [other_prec])):
+        c = kot.Context(device=local_rank, precision=prec, max_iter=args.max_iter)
+        dp = dprobs[0]
+        c.build_features(dp.X, dp.Y, dp.Xf, dp.Yf, dp.sigma, dp.lambda1, dp.lambda2)
+        g0 = torch.zeros(p.l, dtype=torch.float64, device=dev)
+        X0 = torch.zeros(p.l, p.l, dtype=torch.float64, device=dev)
+        r0 = c.ssn_solve(dp.tol, g0, X0, allow_no_convergence=True)
+        finals["mixed" if prec == kot.MIXED else "fp64"] = (g0.cpu().numpy(), X0.cpu().numpy(), r0)
+        c.close()
+
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
     if not args.skip_e2e:
@@ -306,7 +363,7 @@ def main():
     if rank == 0:
         report(args, probs, world, ms_max, ms_local, stats, launches, iters, conv, clocks, peaks,
                None if args.skip_other else (other_prec, o_value, o_ms_max, o_iters, o_conv), e2e,
-               conv_all, tuned)
+               conv_all, tuned, finals)
     if world > 1:
         dist.destroy_process_group()
 
@@ -421,6 +478,218 @@ def batch_bench(args, world, rank, local_rank, dev):
         dist.destroy_process_group()
 
 
+def product_bench(args, world, rank, local_rank, dev):
+    """One FP64-accurate l x l x l product per step through kot_dense_product (C = A B^T): the
+    solve's dominant kernel class on its own, at the workload's l, with the L2 flushed between
+    steps.  --precision mixed: emulated on the tensor cores with --slices slices; fp64: the FP64
+    stream-K GEMM.  This is also the command the ncu captures of that kernel run."""
+    import torch
+    from paper_2310_14087_gb300 import kot
+    l = WORKLOADS[args.workload]["l"]
+    prec = kot.MIXED if args.precision == "mixed" else kot.FP64
+    pieces = -args.slices if prec == kot.MIXED else 0
+    stream = torch.cuda.Stream(device=dev)
+    ctx = kot.Context(device=local_rank, stream=stream.cuda_stream, precision=prec)
+    gen = torch.Generator(device=dev).manual_seed(1234 + rank)
+    A = torch.randn(l, l, dtype=torch.float64, device=dev, generator=gen)
+    B = torch.randn(l, l, dtype=torch.float64, device=dev, generator=gen)
+    Cm = torch.zeros(l, l, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    cls = "gemm_oz" if prec == kot.MIXED else "gemm_f64"
+    for _ in range(args.warmup):
+        ctx.dense_product(l, l, l, 1.0, A, l, 0, B, l, 0, 0.0, Cm, l, pieces)
+    ctx.profile_every(1)
+    ctx.profile(1 << kot.KERNEL_CLASSES.index(cls) | 1 << kot.KERNEL_CLASSES.index("oz_aux"))
+    torch.cuda.synchronize()
+    ms = 0.0
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        ctx.dense_product(l, l, l, 1.0, A, l, 0, B, l, 0, 0.0, Cm, l, pieces)
+        with torch.cuda.stream(stream):
+            b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+    st = ctx.profile_read(kot.KERNEL_CLASSES.index(cls))
+    aux = ctx.profile_read(kot.KERNEL_CLASSES.index("oz_aux"))
+    ctx.profile(0)
+    ref = A @ B.T
+    err = float((Cm - ref).abs().max() / ref.abs().max())
+    peaks = load_peaks()
+    kms = st.ms / max(1, st.launches)
+    if prec == kot.MIXED:
+        peak, src = peaks.get("bf16_tflops", 1934.6), "bf16_tflops (burst) of MEASURED_PEAKS.json: kernel timed alone"
+    else:
+        peak, src = FP64_PEAK_TFLOPS, "FP64 FMA: 152 SMs x 2/clk x 2 flop x 2.07 GHz"
+    achieved = st.flops / max(1, st.launches) / (kms * 1e-3) / 1e12
+    traffic = ROOF_TRAFFIC.get((cls, args.workload, args.slices if prec == kot.MIXED else 0))
+    if rank == 0:
+        print(json.dumps({
+            "metric": "FP64-accurate l x l x l products/s (kot_dense_product)", "method": "product",
+            "value": args.steps / (ms / 1e3), "unit": "products/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "l": l, "precision": args.precision,
+                       "slices": args.slices if prec == kot.MIXED else None,
+                       "rel_max_error_vs_torch_fp64": err, "l2": "flushed before every step"},
+            "roofline": {"kernel": cls, "bound": "tensor" if prec == kot.MIXED else "alu",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "count": "method: 2 l^3 per FP64-accurate product",
+                         "executed_tflops": st.exec_flops / max(1, st.launches) / (kms * 1e-3) / 1e12,
+                         "traffic": traffic, "kernel_us": kms * 1e3,
+                         "aux_us_per_product": aux.ms * 1e3 / max(1, args.steps), "peak_source": src}}),
+              flush=True)
+
+
+def features_bench(args, world, rank, local_rank, dev):
+    """Feature assembly alone (kot_build_features: kernel embeddings, q2 pair sums, Gram matrices,
+    Cholesky) per step on the workload's shape, each kernel class timed with CUDA events."""
+    import torch
+    from paper_2310_14087_gb300 import kot
+    stream = torch.cuda.Stream(device=dev)
+    ctx = kot.Context(device=local_rank, stream=stream.cuda_stream, gram_fp32=int(args.gram_fp32))
+    probs = [kot.DeviceProblem.from_problem(make_problem(args.workload, rank, k), dev)
+             for k in range(args.steps)]
+    warm = kot.DeviceProblem.from_problem(make_problem(args.workload, rank, -1), dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    build = lambda dp: ctx.build_features(dp.X, dp.Y, dp.Xf, dp.Yf, dp.sigma, dp.lambda1, dp.lambda2)
+    for _ in range(args.warmup):
+        build(warm)
+    names = ["embed", "pair_sums", "gram", "cholesky", "gemm_f64"]
+    ctx.profile_every(1)
+    ctx.profile(sum(1 << kot.KERNEL_CLASSES.index(n) for n in names))
+    torch.cuda.synchronize()
+    ms = 0.0
+    for k, dp in enumerate(probs):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        build(dp)
+        with torch.cuda.stream(stream):
+            b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+    stats = {n: ctx.profile_read(kot.KERNEL_CLASSES.index(n)) for n in names}
+    ctx.profile(0)
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    per = {}
+    for n, st in stats.items():
+        if st.launches:
+            per[n] = {"launches": st.launches, "ms": st.ms, "GB/s": st.bytes / (st.ms * 1e-3) / 1e9,
+                      "frac_hbm": st.bytes / (st.ms * 1e-3) / 1e9 / hbm,
+                      "fp64_tflops": st.flops / (st.ms * 1e-3) / 1e12,
+                      "frac_fp64": st.flops / (st.ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "feature assemblies/s (kot_build_features)", "method": "features",
+            "value": args.steps / (ms / 1e3), "unit": "assemblies/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, **config_of(args.workload),
+                       "gram": "fp32" if args.gram_fp32 else "fp64", "l2": "flushed before every step"},
+            "classes": per, "hbm_peak_gbs": hbm, "fp64_peak_tflops": FP64_PEAK_TFLOPS}), flush=True)
+
+
+def eig_bench(args, world, rank, local_rank, dev):
+    """Cold symmetric eigendecompositions (no warm basis: Jacobi sweeps from the identity) of
+    clustered spectra, per size l; the FP64-accurate decomposition behind Eq. (4.4)."""
+    import torch
+    from paper_2310_14087_gb300 import kot
+    stream = torch.cuda.Stream(device=dev)
+    prec = kot.MIXED if args.precision == "mixed" else kot.FP64
+    ctx = kot.Context(device=local_rank, stream=stream.cuda_stream, precision=prec)
+    out = {}
+    for l in [int(x) for x in args.sizes.split(",")]:
+        Z = torch.as_tensor(workloads.clustered_symmetric(l, seed=l), device=dev)
+        P = torch.zeros(l, l, dtype=torch.float64, device=dev)
+        sig = torch.zeros(l, dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            ctx.eig_sym(l, Z, None, P, sig)
+        torch.cuda.synchronize()
+        ms, sweeps = [], []
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            info = ctx.eig_sym(l, Z, None, P, sig)
+            with torch.cuda.stream(stream):
+                b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            sweeps.append(info[0])
+        Zh = Z.cpu().numpy()
+        Ph, sh = P.cpu().numpy(), sig.cpu().numpy()
+        ref = np.linalg.eigvalsh(Zh)
+        out[l] = {"ms_cold": statistics.median(ms), "sweeps": sweeps[0],
+                  "rel_err_eigenvalues": float(np.abs(sh - ref).max() / np.abs(ref).max()),
+                  "orthogonality": float(np.abs(Ph.T @ Ph - np.eye(l)).max())}
+    if rank == 0:
+        print(json.dumps({"metric": "cold symmetric eigendecomposition time per size (kot_eig_sym)",
+                          "method": "eig", "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+                          "steps": args.steps, "warmup": args.warmup, "dtype": "f64", "data": "synthetic",
+                          "config": {"spectrum": "clustered_symmetric (half in 6 clusters of width 1e-9)",
+                                     "precision": args.precision},
+                          "sizes": out}), flush=True)
+
+
+def bootstrap_bench(args, world, rank, local_rank, dev):
+    """--batch bootstrap resamples of one problem that share its filling points: one
+    kot_build_features plus kot_bootstrap_solve (Q, K and R built once), against a feature build
+    and solve per resample.  Both to ||R|| <= 1e-6 (or --max-iter iterations)."""
+    import torch
+    from paper_2310_14087_gb300 import kot
+    prec = kot.MIXED if args.precision == "mixed" else kot.FP64
+    stream = torch.cuda.Stream(device=dev)
+    ctx = kot.Context(device=local_rank, stream=stream.cuda_stream, precision=prec, max_iter=args.max_iter)
+    p = make_problem(args.workload, rank, 0)
+    B = args.batch
+    Xs, Ys = workloads.bootstrap_resamples(p, B, seed=7 + rank)
+    dp = kot.DeviceProblem.from_problem(p, dev)
+    tX, tY = (torch.as_tensor(a, device=dev) for a in (Xs, Ys))
+    G = torch.zeros(B, p.l, dtype=torch.float64, device=dev)
+
+    def shared():
+        ctx.build_features(dp.X, dp.Y, dp.Xf, dp.Yf, dp.sigma, dp.lambda1, dp.lambda2)
+        return ctx.bootstrap_solve(tX, tY, p.tol, G)
+
+    def separate():
+        res = []
+        for b in range(B):
+            ctx.build_features(tX[b], tY[b], dp.Xf, dp.Yf, dp.sigma, dp.lambda1, dp.lambda2)
+            res.append(ctx.ssn_solve(p.tol, G[b], allow_no_convergence=True))
+        return res
+
+    def timed(f):
+        f()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        res = f()
+        with torch.cuda.stream(stream):
+            b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b), res
+
+    ms_sh, res_sh = timed(shared)
+    ms_sep, res_sep = timed(separate)
+    its = [r.iters for r in res_sh]
+    if rank == 0:
+        print(json.dumps({
+            "metric": "bootstrap solves/s with shared filling points (kot_bootstrap_solve)",
+            "method": "bootstrap", "value": B / (ms_sh / 1e3), "unit": "solves/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, **config_of(args.workload), "resamples": B,
+                       "precision": args.precision, "max_iter": args.max_iter, "iters": its,
+                       "converged": sum(int(r.status == kot.OK) for r in res_sh)},
+            "ms_shared": ms_sh, "ms_separate": ms_sep, "separate_value": B / (ms_sep / 1e3),
+            "same_iterations": its == [r.iters for r in res_sep]}), flush=True)
+
+
 def end_to_end(args, p, main_prec, world, dev, local_rank):
     """The same problems through the C ABI with HOST buffers: the library copies each step's
     inputs in and gamma out inside the timed region."""
@@ -458,8 +727,22 @@ def end_to_end(args, p, main_prec, world, dev, local_rank):
     return {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 
+def errors_vs_oracle(F, ref, finals):
+    """Distance of each form's result from the oracle's solve of the same problem to the same
+    tolerance: relative error of f(gamma) and of gamma (max norm over max |gamma|), and ||R|| as
+    the oracle evaluates it at the returned iterate."""
+    from oracle import kot_oracle as ko
+    out = {}
+    for name, (g, X, r) in finals.items():
+        out[name] = {"rel_err_objective": abs(r.objective - ref.objective) / abs(ref.objective),
+                     "rel_err_gamma": float(np.abs(g - ref.gamma).max() / np.abs(ref.gamma).max()),
+                     "residual_reported": r.residual, "residual_by_oracle": ko.residual(F, g, X).norm,
+                     "iters": r.iters, "oracle_iters": ref.iters}
+    return out
+
+
 def report(args, probs, world, ms_max, ms_local, stats, launches, iters, conv, clocks, peaks, other,
-           e2e, conv_all, tuned=None):
+           e2e, conv_all, tuned=None, finals=None):
     from paper_2310_14087_gb300 import kot
     value = conv_all / (ms_max / 1e3)          # converged solves per second, all ranks
     stats, breakdown = stats
@@ -470,7 +753,8 @@ def report(args, probs, world, ms_max, ms_local, stats, launches, iters, conv, c
     if s.launches == 0:
         dom = None                         # nothing was timed (--profile none)
     if dom == "gemm_oz":
-        # executed BF16 tensor work (slice-pair products) against the sustained BF16 peak
+        # the method's work (2MNK per FP64-accurate product) against the sustained BF16 peak;
+        # the executed BF16 slice-pair work is reported beside it
         bound, unit = "tensor", "TFLOP/s"
         peak = peaks.get("bf16_tflops_sustained", 1713.0)
         peak_src = "bf16_tflops_sustained of MEASURED_PEAKS.json (kernel timed inside a long step)"
@@ -480,12 +764,15 @@ def report(args, probs, world, ms_max, ms_local, stats, launches, iters, conv, c
     roofline = None
     if dom is not None:
         achieved = (s.flops / s.launches) / (per_launch_ms * 1e-3) / 1e12
-        traffic = ROOF_TRAFFIC.get((dom, args.workload))
+        executed = (s.exec_flops / s.launches) / (per_launch_ms * 1e-3) / 1e12
+        traffic = ROOF_TRAFFIC.get((dom, args.workload, 6 if dom == "gemm_oz" else 0))
         roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
                     "unit": unit, "frac": achieved / peak, "traffic": traffic,
-                    "traffic_note": None if traffic is None else
-                    "ncu dram__bytes_read+write of one 300x300x300 six-slice launch (bytes)",
-                    "traffic_last_capture": ROOF_TRAFFIC_LAST.get((dom, args.workload)),
+                    "count": "method: 2MNK flops per FP64-accurate product",
+                    "executed_tflops": executed, "executed_frac": executed / peak,
+                    "traffic_note": "ncu dram__bytes_read+write per launch of the standalone l x l x l "
+                                    "six-slice product (bench.py --method product)" if traffic else
+                                    "no capture of the current kernel: bench.py --method product under ncu",
                     "launches_timed": s.launches, "timed_one_in": PROFILE_EVERY if args.profile == "roofline" else 1,
                     "avg_launch_us": per_launch_ms * 1e3,
                     "share_of_step": s.ms * (PROFILE_EVERY if args.profile == "roofline" else 1) / ms_local,
@@ -512,8 +799,29 @@ def report(args, probs, world, ms_max, ms_local, stats, launches, iters, conv, c
         "kernels_one_untimed_step": {k: {"launches": v.launches, "ms": round(v.ms, 3)}
                                      for k, v in breakdown.items() if v.launches},
     }
+    mv = breakdown.get("schur_matvec")
+    if mv is not None and mv.launches:
+        mpk = peaks.get("bf16_tflops_sustained", 1713.0) if args.precision == "mixed" else FP64_PEAK_TFLOPS
+        line["matvec"] = {
+            "what": "one Schur-operator application of CG (Algorithm 1), one untimed step",
+            "launches": mv.launches, "us_per_matvec": 1e3 * mv.ms / mv.launches,
+            "fmv_tflops": mv.flops / (mv.ms * 1e-3) / 1e12,
+            "exec_tflops": mv.exec_flops / (mv.ms * 1e-3) / 1e12,
+            "frac_fmv": mv.flops / (mv.ms * 1e-3) / 1e12 / mpk, "peak": mpk,
+            "count": "F_mv = (4/3) l^3 + 8 min(|alpha|,|alpha-bar|) l^2 + 2 l^2 (algorithmic); executed: "
+                     "the eigenbasis form, 4 min(|alpha|,|alpha-bar|) l^2 + 2 l^2"}
+    gr = breakdown.get("gram")
+    if gr is not None and gr.launches:
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        gbs = gr.bytes / (gr.ms * 1e-3) / 1e9
+        line["gram"] = {"what": "Gram matrices Q and K (k_gram), one untimed step", "ms": gr.ms,
+                        "GB/s": gbs, "frac_hbm": gbs / hbm, "hbm_peak": hbm,
+                        "fp64_tflops": gr.flops / (gr.ms * 1e-3) / 1e12,
+                        "frac_fp64": gr.flops / (gr.ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
     if not args.no_cpu_baseline and world == 1:
-        tcpu, r = oracle_solve(probs[0])
+        tcpu, r, F = oracle_solve(probs[0], with_features=True)
+        if finals:
+            line["errors_vs_oracle"] = errors_vs_oracle(F, r, finals)
         line["cpu_baseline"] = {
             "value": (1.0 if r.converged else 0.0) / tcpu, "unit": "solves/s",
             "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
@@ -521,6 +829,7 @@ def report(args, probs, world, ms_max, ms_local, stats, launches, iters, conv, c
             "sample": f"1 full solve of {args.workload} (the step-0 problem: features + "
                       f"Algorithm 2, {r.iters} iterations, converged={r.converged}), "
                       "NumPy/LAPACK FP64, default BLAS threads"}
+        line["cpu_baseline"]["one_core"] = one_core_line(args.workload)
     print(json.dumps(line), flush=True)
 
 

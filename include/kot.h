@@ -89,6 +89,9 @@ typedef struct {
                               both): 0 = conjugate gradients (default), 1 = symmetric QMR
                               (Freund-Nachtigal, no preconditioner); both stop on Eq. (4.3)
                               measured with the true residual and cap at cg_max_iter */
+  int gram_fp32;           /* kot_build_features: 1 = the Gram matrices Q and K (Sec. 3) from FP32
+                              distances and exponentials (entries ~1e-7 relative to FP64; the
+                              embeddings, q2, z and the Cholesky stay FP64); 0 = FP64 (default) */
 } kot_options;
 
 typedef struct {
@@ -215,6 +218,21 @@ typedef struct {
  * in problem order (KOT_OK if all converged); each res[i].status is per problem. */
 kot_status kot_batch_solve(kot_ctx* ctx, int B, const kot_problem* probs, kot_result* res);
 
+/* Bootstrap resamples with shared filling points (the bandwidth and bootstrap settings of Sec. 5
+ * keep the filling points fixed while the samples change).  After kot_build_features(ctx, d, ...,
+ * l, Xf, Yf, sigma, lambda1, lambda2), solves B problems whose samples are the resamples
+ * Xs[b], Ys[b] (b < B; each n x d, stored one after another: Xs is B x n x d) with the context's
+ * filling points, sigma, lambda1 and lambda2.  Q, K and the Cholesky factor R (Sec. 3), the
+ * jitter and the EG step bound depend on the filling points only, so they are built once (by
+ * kot_build_features) and shared; each resample rebuilds the kernel embeddings w_mu, w_nu, q2 and
+ * z (Sec. 3) and runs Algorithm 2 from zero to ||R(w)|| <= tol.  gamma_out: B x l, resample b's
+ * gamma in row b.  res: B host results.  Arrays follow the context's pointer mode.  After the
+ * call the context holds the last resample's problem (kot_potentials uses its samples).
+ * Returns KOT_ERR_STATE without kot_build_features before it, else the first non-OK status in
+ * resample order (each res[b].status is per resample).  n may differ from kot_build_features's. */
+kot_status kot_bootstrap_solve(kot_ctx* ctx, int B, int n, const double* Xs, const double* Ys, double tol,
+                               double* gamma_out, kot_result* res);
+
 /* ---- building block: symmetric eigen-decomposition (Sec. 4.1, Eq. (4.4)) ----
  * The projection onto the PSD cone and the weights Omega of the generalized Jacobian are read
  * off Z = P diag(sig) P^T.  Z: l x l, row-major, symmetric (the library uses (Z + Z^T)/2).
@@ -266,15 +284,22 @@ kot_status kot_autotune(kot_ctx* ctx, int l, int* choice);
  * decomposition), 2 reserved (unused), 3 kernel mean embeddings and potentials,
  * 4 embedding-norm pair sums, 5 Gram matrices Q and K, 6 Cholesky diagonal block,
  * 7 tensor-core (tcgen05) GEMM tiles, 8 eigenbasis refinement correction, 9 FP64-emulating
- * tensor-core GEMM (k_oz_gemm), 10 its slicing and finalize kernels.
+ * tensor-core GEMM (k_oz_gemm), 10 its slicing and finalize kernels, 11 one application of the
+ * Schur operator H p = Q p/(2 lambda2) + mu p + Phi(T[Phi*(p)]) inside CG (Algorithm 1; all of
+ * its launches between one event pair).
  * kot_profile(ctx, mask) turns on timing of the classes whose bit is set in mask (0 = off) and
  * clears the statistics.  While on, every launch of an enabled class is bracketed by CUDA events
  * on the context's stream.  kot_profile_read fills, for class cls, the number of launches, the
- * summed event time in milliseconds, and the summed algorithmic flops and bytes of those
- * launches (the counts each launch site states for its arithmetic and its compulsory traffic). */
+ * summed event time in milliseconds, the summed algorithmic flops and bytes of those launches
+ * (the counts each launch site states for the method's arithmetic and its compulsory traffic),
+ * and the summed flops they executed.  Algorithmic flops are the method's count: 2MNK for an
+ * FP64-accurate product however it is computed (class 9 executes 2MNK per BF16 slice pair), and
+ * for class 11 F_mv = (4/3) l^3 + 8 a l^2 + 2 l^2 with a = min(|alpha|, |alpha-bar|) (Phi* and Phi
+ * on the triangular factor, T_k in the cost-reduced forms of Sec. 4.3, Q p); class 11 executes
+ * the eigenbasis form, 4 a l^2 + 2 l^2 in FP64-accurate terms. */
 typedef struct {
   long long launches;
-  double ms, flops, bytes;
+  double ms, flops, bytes, exec_flops;
 } kot_kernel_stats;
 
 kot_status kot_profile(kot_ctx* ctx, int mask);

@@ -39,10 +39,10 @@ void Profiler::begin(cudaStream_t st, int cls, cudaEvent_t* a) {
   KOT_CUDA(cudaEventRecord(*a, st));
 }
 
-void Profiler::end(cudaStream_t st, int cls, cudaEvent_t a, double fl, double by) {
+void Profiler::end(cudaStream_t st, int cls, cudaEvent_t a, double fl, double by, double ex) {
   cudaEvent_t b = get_event();
   if (cudaEventRecord(b, st) != cudaSuccess) return;
-  pending.push_back({cls, a, b, fl, by});
+  pending.push_back({cls, a, b, fl, by, ex});
   if (pending.size() > 4096) collect();
 }
 
@@ -54,6 +54,7 @@ void Profiler::collect() {
       ms[q.cls] += t;
       flops[q.cls] += q.flops;
       bytes[q.cls] += q.bytes;
+      exec[q.cls] += q.exec;
     }
     pool.push_back(q.a);
     pool.push_back(q.b);
@@ -63,7 +64,7 @@ void Profiler::collect() {
 
 void Profiler::reset() {
   collect();
-  for (int i = 0; i < KC_COUNT; ++i) launches[i] = seen[i] = 0, ms[i] = flops[i] = bytes[i] = 0.0;
+  for (int i = 0; i < KC_COUNT; ++i) launches[i] = seen[i] = 0, ms[i] = flops[i] = bytes[i] = exec[i] = 0.0;
 }
 
 void Profiler::release() {
@@ -591,6 +592,14 @@ __global__ void k_xpby_ratio(size_t n, const double* __restrict__ x, const doubl
     y[i] = fma(b, y[i], x[i]);
 }
 
+__global__ void k_square(size_t n, const double* __restrict__ x, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = x[i] * x[i];
+}
+
 __global__ void k_fill(size_t n, double v, double* __restrict__ out) {
   pdl_wait();
   pdl_trigger();
@@ -830,6 +839,16 @@ void eig_norms(cudaStream_t st, size_t n1, const double* x, int rows, int cols, 
   launch_pdl(k_eig_norms, dim3(nbk), dim3(256), 0, st, n1, x, rows, cols, ld, nb, A, W, base, partial);
   launch_pdl(k_sum_pairs, dim3(1), dim3(256), 0, st, nbk, partial, out2);
   KOT_LAUNCHED(2);
+}
+
+void sum_pairs(cudaStream_t st, int nb, const double* partial, double* out2) {
+  launch_pdl(k_sum_pairs, dim3(1), dim3(256), 0, st, nb, partial, out2);
+  KOT_CHECK_LAUNCH();
+}
+
+void square_elems(cudaStream_t st, size_t n, const double* x, double* out) {
+  launch_pdl(k_square, dim3(elementwise_grid(n)), dim3(256), 0, st, n, x, out);
+  KOT_CHECK_LAUNCH();
 }
 
 void hmatvec(cudaStream_t st, int n, double alpha, const double* A, const double* x, double mu,

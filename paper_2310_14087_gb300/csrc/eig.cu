@@ -390,53 +390,15 @@ __global__ void __launch_bounds__(kCoopThreads) k_jacobi_coop(CoopArgs<T> a) {
       const T* rc = rot[gr & 1];
       T* rn = rot[(gr + 1) & 1];
       const int rnext = (r + 1 == lp - 1) ? 0 : r + 1;
-      const int nA = half * half, nV = l * half, nN = half;
-      // next-round angle items are dealt round-robin over the CTAs (item k -> CTA k mod grid,
-      // thread k / grid): a few FP64 divide/square-root chains per SM instead of all of them on
-      // the one or two SMs a contiguous range would land on (FP64 issues ~2 ops/clk per SM)
-      for (int it0 = (int)(threadIdx.x * nb + blockIdx.x); it0 < nA + nV + nN; it0 += (int)gstride) {
-        const int it = (it0 < nN) ? nA + nV + it0 : it0 - nN;
-        if (it < nA) {
-          const int ia = it / half, ib = it - ia * half;
-          if (ib < ia) continue;
-          int pa, qa, pb, qb;
-          round_pair(lp, r, ia, pa, qa);
-          round_pair(lp, r, ib, pb, qb);
-          const T ca = __ldcg(rc + 2 * ia), sa = __ldcg(rc + 2 * ia + 1);
-          const T cb = __ldcg(rc + 2 * ib), sb = __ldcg(rc + 2 * ib + 1);
-          T n00, n01, n10, n11;
-          rot_block<T>(ca, sa, cb, sb, __ldcg(src + (size_t)pa * lp + pb), __ldcg(src + (size_t)pa * lp + qb),
-                       __ldcg(src + (size_t)qa * lp + pb), __ldcg(src + (size_t)qa * lp + qb),
-                       n00, n01, n10, n11);
-          if (ia == ib) {
-            dst[(size_t)pa * lp + pa] = n00;
-            dst[(size_t)qa * lp + qa] = n11;
-            dst[(size_t)pa * lp + qa] = n01;
-            dst[(size_t)qa * lp + pa] = n01;
-          } else {
-            dst[(size_t)pa * lp + pb] = n00;
-            dst[(size_t)pa * lp + qb] = n01;
-            dst[(size_t)qa * lp + pb] = n10;
-            dst[(size_t)qa * lp + qb] = n11;
-            dst[(size_t)pb * lp + pa] = n00;
-            dst[(size_t)qb * lp + pa] = n01;
-            dst[(size_t)pb * lp + qa] = n10;
-            dst[(size_t)qb * lp + qa] = n11;
-          }
-        } else if (it < nA + nV) {
-          const int v = it - nA;
-          const int i = v / half, b = v - i * half;
-          int pb, qb;
-          round_pair(lp, r, b, pb, qb);
-          const T cb = __ldcg(rc + 2 * b), sb = __ldcg(rc + 2 * b + 1);
-          if (sb == T(0) && cb == T(1)) continue;
-          T* row = a.V + (size_t)i * lp;
-          const T vp = __ldcg(row + pb), vq = __ldcg(row + qb);
-          row[pb] = cb * vp - sb * vq;
-          row[qb] = sb * vp + cb * vq;
-        } else {
+      const int nAu = half * (half + 1) / 2, nV = l * half, nN = half;
+      // The round's items: the 2 x 2 blocks (ia, ib >= ia) of A, the (row, pair) items of V and
+      // the next round's angles.  A and V items are taken contiguously along the grid (row by
+      // row, so the lanes of a warp touch neighbouring columns); the angle items are dealt
+      // round-robin over the CTAs (item k -> CTA k mod grid, thread k / grid): a few FP64
+      // divide/square-root chains per SM instead of all of them on the one or two SMs a
+      // contiguous range would land on (FP64 issues ~2 ops/clk per SM).
+      for (int k = (int)(threadIdx.x * nb + blockIdx.x); k < nN; k += (int)gstride) {
           // angle of next-round pair k from the values this round writes, recomputed here
-          const int k = it - nA - nV;
           int pn, qn;
           round_pair(lp, rnext, k, pn, qn);
           const int sp = slot_of(lp, r, pn), sq = slot_of(lp, r, qn);
@@ -465,6 +427,54 @@ __global__ void __launch_bounds__(kCoopThreads) k_jacobi_coop(CoopArgs<T> a) {
           rot_angle<T>(app, aqq, apq, c, s);
           rn[2 * k] = c;
           rn[2 * k + 1] = s;
+      }
+      for (size_t it = gtid; it < (size_t)nAu + nV; it += gstride) {
+        if (it < (size_t)nAu) {
+          // upper-triangle block index -> (ia, ib): row ia holds blocks ia .. half - 1 and starts
+          // at ia half - ia (ia - 1)/2
+          const int t = (int)it;
+          const float bq = 2.0f * half + 1.0f;
+          int ia = (int)((bq - sqrtf(fmaxf(bq * bq - 8.0f * t, 0.0f))) * 0.5f);
+          if (ia < 0) ia = 0;
+          while (ia > 0 && ia * half - ia * (ia - 1) / 2 > t) --ia;
+          while ((ia + 1) * half - (ia + 1) * ia / 2 <= t) ++ia;
+          const int ib = ia + (t - (ia * half - ia * (ia - 1) / 2));
+          int pa, qa, pb, qb;
+          round_pair(lp, r, ia, pa, qa);
+          round_pair(lp, r, ib, pb, qb);
+          const T ca = __ldcg(rc + 2 * ia), sa = __ldcg(rc + 2 * ia + 1);
+          const T cb = __ldcg(rc + 2 * ib), sb = __ldcg(rc + 2 * ib + 1);
+          T n00, n01, n10, n11;
+          rot_block<T>(ca, sa, cb, sb, __ldcg(src + (size_t)pa * lp + pb), __ldcg(src + (size_t)pa * lp + qb),
+                       __ldcg(src + (size_t)qa * lp + pb), __ldcg(src + (size_t)qa * lp + qb),
+                       n00, n01, n10, n11);
+          if (ia == ib) {
+            dst[(size_t)pa * lp + pa] = n00;
+            dst[(size_t)qa * lp + qa] = n11;
+            dst[(size_t)pa * lp + qa] = n01;
+            dst[(size_t)qa * lp + pa] = n01;
+          } else {
+            dst[(size_t)pa * lp + pb] = n00;
+            dst[(size_t)pa * lp + qb] = n01;
+            dst[(size_t)qa * lp + pb] = n10;
+            dst[(size_t)qa * lp + qb] = n11;
+            dst[(size_t)pb * lp + pa] = n00;
+            dst[(size_t)qb * lp + pa] = n01;
+            dst[(size_t)pb * lp + qa] = n10;
+            dst[(size_t)qb * lp + qa] = n11;
+          }
+        } else {
+          const int v = (int)(it - nAu);
+          const int i = v / half, b = v - i * half;
+          int pb, qb;
+          round_pair(lp, r, b, pb, qb);
+          const T cb = __ldcg(rc + 2 * b), sb = __ldcg(rc + 2 * b + 1);
+          if (!(sb == T(0) && cb == T(1))) {
+          T* row = a.V + (size_t)i * lp;
+          const T vp = __ldcg(row + pb), vq = __ldcg(row + qb);
+          row[pb] = cb * vp - sb * vq;
+          row[qb] = sb * vp + cb * vq;
+          }
         }
       }
       if (!grid_barrier(a.bar, nb, epoch, a.err)) return;

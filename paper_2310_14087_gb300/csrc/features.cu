@@ -157,11 +157,14 @@ __global__ void k_sum_scaled(int m, const double* __restrict__ partial, double s
   if (t == 0) *out = red[0] * scale;
 }
 
-// Q_ij = k(xf_i, xf_j) + k(yf_i, yf_j), K_ij = k((xf_i, yf_i), (xf_j, yf_j)).
+// Q_ij = k(xf_i, xf_j) + k(yf_i, yf_j), K_ij = k((xf_i, yf_i), (xf_j, yf_j)).  Both are symmetric
+// and (a - b)^2 = (b - a)^2 exactly, so each pair i <= j is evaluated once and stored at both
+// positions (half the FP64 work of the full square, which bounds this kernel); blocks wholly below
+// the diagonal exit at once.
 __global__ void k_gram(int l, int d, const double* __restrict__ Xf, const double* __restrict__ Yf,
                        double inv2s2, double* __restrict__ Q, double* __restrict__ K) {
   const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
-  if (i >= l || j >= l) return;
+  if (i >= l || j >= l || j < i) return;
   double dx = 0.0, dy = 0.0;
   for (int c = 0; c < d; ++c) {
     double a = Xf[(size_t)i * d + c] - Xf[(size_t)j * d + c];
@@ -171,8 +174,78 @@ __global__ void k_gram(int l, int d, const double* __restrict__ Xf, const double
     double b = Yf[(size_t)i * d + c] - Yf[(size_t)j * d + c];
     dy = fma(b, b, dy);
   }
-  Q[(size_t)i * l + j] = exp(-dx * inv2s2) + exp(-dy * inv2s2);
-  K[(size_t)i * l + j] = exp(-(dx + dy) * inv2s2);
+  const double q = exp(-dx * inv2s2) + exp(-dy * inv2s2), k = exp(-(dx + dy) * inv2s2);
+  Q[(size_t)i * l + j] = q;
+  K[(size_t)i * l + j] = k;
+  if (j != i) {
+    Q[(size_t)j * l + i] = q;
+    K[(size_t)j * l + i] = k;
+  }
+}
+
+// The same Gram matrices with the distances and exponentials in FP32 (the stored values are the
+// FP32 results, exactly, in FP64): FP32 issues about 32x the FP64 rate here, so this build is
+// bound by its stores instead of the FP64 pipe.  A block covers a 64 x 64 tile of pairs with 256
+// threads, each a 4 x 4 register tile; the tile's 64 + 64 points are staged in shared memory as
+// FP32, GW coordinates at a time.  Only tiles that reach the diagonal or above run, and each pair
+// i <= j is stored at both positions.
+constexpr int GT = 64, GW = 32;
+__global__ void __launch_bounds__(256) k_gram_f32(int l, int d, const double* __restrict__ Xf,
+                                                  const double* __restrict__ Yf, float inv2s2,
+                                                  double* __restrict__ Q, double* __restrict__ K) {
+  const int bi = blockIdx.y * GT, bj = blockIdx.x * GT;
+  if (bj + GT <= bi) return;                       // wholly below the diagonal
+  __shared__ float pr[2][GW][GT + 1], pc[2][GW][GT + 1];   // [x or y][coordinate][point]
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads, 4 x 4 pairs each
+  float dx[4][4] = {}, dy[4][4] = {};
+  for (int c0 = 0; c0 < d; c0 += GW) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 2 * GW * GT; e += 256) {
+      const int h = e / (GW * GT), r = e % (GW * GT), pt = r / GW, c = r % GW;
+      const double* S = h ? Yf : Xf;
+      const int gi = bi + pt, gj = bj + pt, cc = c0 + c;
+      pr[h][c][pt] = (gi < l && cc < d) ? (float)S[(size_t)gi * d + cc] : 0.0f;
+      pc[h][c][pt] = (gj < l && cc < d) ? (float)S[(size_t)gj * d + cc] : 0.0f;
+    }
+    __syncthreads();
+    const int cn = min(GW, d - c0);
+    for (int c = 0; c < cn; ++c) {
+      float ax[4], ay[4], bx[4], by[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        ax[u] = pr[0][c][ty * 4 + u];
+        ay[u] = pr[1][c][ty * 4 + u];
+        bx[u] = pc[0][c][tx * 4 + u];
+        by[u] = pc[1][c][tx * 4 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const float ex = ax[u] - bx[v], ey = ay[u] - by[v];
+          dx[u][v] = fmaf(ex, ex, dx[u][v]);
+          dy[u][v] = fmaf(ey, ey, dy[u][v]);
+        }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = bi + ty * 4 + u;
+    if (i >= l) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int j = bj + tx * 4 + v;
+      if (j >= l || j < i) continue;
+      const double q = (double)(expf(-dx[u][v] * inv2s2) + expf(-dy[u][v] * inv2s2));
+      const double k = (double)expf(-(dx[u][v] + dy[u][v]) * inv2s2);
+      Q[(size_t)i * l + j] = q;
+      K[(size_t)i * l + j] = k;
+      if (j != i) {
+        Q[(size_t)j * l + i] = q;
+        K[(size_t)j * l + i] = k;
+      }
+    }
+  }
 }
 
 // c_i = ||xf_i - yf_i||^2 ; z_i = w_mu_i + w_nu_i - lambda2 c_i
@@ -194,22 +267,30 @@ __global__ void k_cost_z(int l, int d, const double* __restrict__ Xf, const doub
 // ------------------------------------------------------------------ blocked upper Cholesky
 constexpr int CB = 32;
 
-// Factor the diagonal block A[k0:k0+nb, k0:k0+nb] (upper) in shared memory.
+// Factor the diagonal block A[k0:k0+nb, k0:k0+nb] (upper) in shared memory.  Each pivot's square
+// root and reciprocal are formed once, by one thread, and the row is scaled by multiplication: this
+// SM issues about two FP64 operations per clock, so a square root or division in every thread
+// would cost thousands of cycles per pivot.
 __global__ void k_chol_diag(int l, int k0, double* __restrict__ A, int* __restrict__ info) {
   __shared__ double a[CB][CB + 1];
+  __shared__ double rinv[2];   // [sqrt(pivot), 1/sqrt(pivot)]
   const int nb = min(CB, l - k0);
   const int tx = threadIdx.x, ty = threadIdx.y;      // 32 x 32
   if (tx < nb && ty < nb) a[ty][tx] = A[(size_t)(k0 + ty) * l + k0 + tx];
   __syncthreads();
   for (int p = 0; p < nb; ++p) {
-    double piv = a[p][p];
-    __syncthreads();
-    if (!(piv > 0.0) || !isfinite(piv)) {
-      if (tx == 0 && ty == 0 && *info == 0) *info = k0 + p + 1;
-      piv = 1.0;                                         // keep going; result is discarded
+    if (tx == 0 && ty == 0) {
+      double piv = a[p][p];
+      if (!(piv > 0.0) || !isfinite(piv)) {
+        if (*info == 0) *info = k0 + p + 1;
+        piv = 1.0;                                       // keep going; result is discarded
+      }
+      const double r = sqrt(piv);
+      rinv[0] = r;
+      rinv[1] = 1.0 / r;
     }
-    const double r = sqrt(piv);
-    if (ty == 0 && tx >= p && tx < nb) a[p][tx] = (tx == p) ? r : a[p][tx] / r;
+    __syncthreads();
+    if (ty == 0 && tx >= p && tx < nb) a[p][tx] = (tx == p) ? rinv[0] : a[p][tx] * rinv[1];
     __syncthreads();
     if (ty > p && tx >= ty && tx < nb && ty < nb) a[ty][tx] -= a[p][ty] * a[p][tx];
     __syncthreads();
@@ -222,10 +303,13 @@ __global__ void k_chol_panel(int l, int k0, double* __restrict__ A) {
   const int nb = min(CB, l - k0);
   const int col = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
   __shared__ double r[CB][CB + 1];
+  __shared__ double dinv[CB];   // reciprocals of the diagonal (one division per pivot, not per column)
   for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
     int i = e / CB, j = e % CB;
     r[i][j] = (i < nb && j < nb) ? A[(size_t)(k0 + i) * l + k0 + j] : 0.0;
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < CB; i += blockDim.x) dinv[i] = i < nb ? 1.0 / r[i][i] : 0.0;
   __syncthreads();
   if (col >= l) return;
   double x[CB];
@@ -234,7 +318,7 @@ __global__ void k_chol_panel(int l, int k0, double* __restrict__ A) {
     if (i < nb) {
       double v = A[(size_t)(k0 + i) * l + col];
       for (int k = 0; k < i; ++k) v -= r[k][i] * x[k];
-      x[i] = v / r[i][i];
+      x[i] = v * dinv[i];
       A[(size_t)(k0 + i) * l + col] = x[i];
     }
   }
@@ -334,13 +418,23 @@ void pair_mean_f64(cudaStream_t st, int n, int d, const double* S, double inv2s2
 
 void gram_f64(cudaStream_t st, int l, int d, const double* Xf, const double* Yf, double inv2s2,
               double lambda2, const double* w_mu, const double* w_nu, double* Q, double* K,
-              double* c, double* z) {
+              double* c, double* z, bool fp32) {
   {
-    ProfScope ps(st, KC_GRAM, (double)l * l * (6.0 * d + 5.0), 8.0 * (2.0 * l * d + 2.0 * (double)l * l));
-    k_gram<<<dim3(cdiv(l, 32), cdiv(l, 8)), dim3(32, 8), 0, st>>>(l, d, Xf, Yf, inv2s2, Q, K);
+    // flops: the pairs i <= j, 6d + 5 each; bytes: the points in, Q and K out
+    ProfScope ps(st, KC_GRAM, (double)l * (l + 1) / 2.0 * (6.0 * d + 5.0), 8.0 * (2.0 * l * d + 2.0 * (double)l * l));
+    if (fp32)
+      k_gram_f32<<<dim3(cdiv(l, GT), cdiv(l, GT)), 256, 0, st>>>(l, d, Xf, Yf, (float)inv2s2, Q, K);
+    else
+      k_gram<<<dim3(cdiv(l, 32), cdiv(l, 8)), dim3(32, 8), 0, st>>>(l, d, Xf, Yf, inv2s2, Q, K);
   }
   k_cost_z<<<cdiv(l, 128), 128, 0, st>>>(l, d, Xf, Yf, lambda2, w_mu, w_nu, c, z);
   KOT_LAUNCHED(2);
+}
+
+void cost_z_f64(cudaStream_t st, int l, int d, const double* Xf, const double* Yf, double lambda2,
+                const double* w_mu, const double* w_nu, double* c, double* z) {
+  k_cost_z<<<cdiv(l, 128), 128, 0, st>>>(l, d, Xf, Yf, lambda2, w_mu, w_nu, c, z);
+  KOT_CHECK_LAUNCH();
 }
 
 void cholesky_upper_f64(cudaStream_t st, int l, double* A, double eps, int* info) {
@@ -355,7 +449,7 @@ void cholesky_upper_f64(cudaStream_t st, int l, double* A, double eps, int* info
     KOT_CHECK_LAUNCH();
     const int rest = l - k0 - nb;
     if (rest <= 0) break;
-    k_chol_panel<<<cdiv(rest, 64), 64, 0, st>>>(l, k0, A);
+    k_chol_panel<<<cdiv(rest, 32), 32, 0, st>>>(l, k0, A);   // one warp per block: more SMs
     KOT_CHECK_LAUNCH();
     // trailing update of the upper triangle: A[k1:, k1:] -= P^T P, P = A[k0:k1, k1:]
     double* Pp = A + (size_t)k0 * l + k0 + nb;

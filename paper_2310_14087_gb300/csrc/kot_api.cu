@@ -79,7 +79,8 @@ struct kot_ctx {
   ResState rw, rv, rt;
   EigSlot ew, ev, et, e1, e2;
   DevBuf<double> M1, M2, M3, M4, M5, M6, TU, TV, TW, TG;
-  DevBuf<double> Cb, A2, Wx;   // eigenbasis CG: P^T R, P^T at2 P, alpha rows of P^T T[Phi*(x)] P
+  DevBuf<double> Cb, A2, Wx;   // eigenbasis CG: P^T R, P^T at2 P, the carried rows for x (see schur_eig)
+  DevBuf<double> KK, H0, phia2;   // Kt o Kt (Kt = R^T R); Q/(2 lambda2) + KK/mu; Phi(at2)
   DevBuf<double> v1, v2, v3, v4, v5, v6, w1, w2, w3;
   DevBuf<double> Fvg, FvX;     // F(v) of the EG iterate, from its last residual evaluation
   bool fv_valid = false;
@@ -145,12 +146,12 @@ void ensure(kot_ctx* C, int l) {
   for (DevBuf<double>* b : {&C->Q, &C->K, &C->R, &C->X, &C->vX, &C->tX, &C->dX, &C->M1, &C->M2,
                             &C->M3, &C->M4, &C->M5, &C->M6, &C->TU, &C->TV, &C->TW, &C->TG,
                             &C->Cb, &C->A2, &C->Wx, &C->rw.r2, &C->rv.r2, &C->rt.r2, &C->FvX,
-                            &C->Plast})
+                            &C->Plast, &C->KK, &C->H0})
     b->alloc(L2);
   C->Fvg.alloc(L);
   for (DevBuf<double>* b : {&C->z, &C->w_mu, &C->w_nu, &C->c, &C->g, &C->vg, &C->tg, &C->dg,
                             &C->v1, &C->v2, &C->v3, &C->v4, &C->v5, &C->v6, &C->w1, &C->w2,
-                            &C->w3, &C->rw.r1,
+                            &C->w3, &C->rw.r1, &C->phia2,
                             &C->rv.r1, &C->rt.r1})
     b->alloc(L);
   for (EigSlot* e : {&C->ew, &C->ev, &C->et, &C->e1, &C->e2}) {
@@ -388,10 +389,34 @@ void cg_gemm(kot_ctx* C, bool ta, bool tb, int M, int N, int K, const double* A,
     gemm_acc(C->st, ozp(C), ta, tb, M, N, K, 1.0, A, l, B, l, s, 0.0, out, l, 0);
 }
 
+// Complement form (|alpha| > |alpha-bar|, the last paragraph of Sec. 4.3): with Psi' = E/mu - Psi,
+// which vanishes on alpha x alpha, Psi o V = V/mu - Psi' o V and, for orthogonal P,
+// diag(Cb^T V Cb) = (Kt o Kt) p with Kt = R^T R.  So Phi(T[Phi*(p)]) = (Kt o Kt) p/mu
+// - 2 diag(Cb_abar^T W' Cb), W' = the alpha-bar rows U = Cb_abar diag(p) Cb^T weighted by 1/(2 mu)
+// on alpha-bar columns and 1/mu - xi on alpha columns: two |alpha-bar| x l x l products plus the
+// matvec with H0 = Q/(2 lambda2) + (Kt o Kt)/mu, formed once per direction.  Either way one
+// operator application costs 2 min(|alpha|, |alpha-bar|) l^2 multiply-adds in products.
+// Out: W = the carried rows for p -- the weighted alpha rows (G + G^T form) or the unweighted
+// alpha-bar rows U (complement form) -- and Hp = Q p/(2 lambda2) + mu p + Phi(T[Phi*(p)]);
+// Y: rows x l scratch.
+bool complement_form(const EigSlot& e, int l) { return l - e.nb > e.nb; }
+
 void schur_eig(kot_ctx* C, const EigSlot& e, double mu, const double* p, double* W, double* Y, double* Hp) {
   const int l = C->l, nb = e.nb, na = l - nb;
   cudaStream_t st = C->st;
   const double* Cb = C->Cb.p;
+  if (complement_form(e, l)) {
+    if (nb == 0) {
+      fill(st, l, 0.0, C->v5.p);
+    } else {
+      cg_gemm(C, false, true, nb, l, l, Cb, Cb, p, W);       // U = Cb_abar diag(p) Cb^T
+      t_weights(st, l, nb, e.sig.p, mu, 1, Y, W);            // W' = weights o U
+      cg_gemm(C, false, false, nb, l, l, Y, Cb, nullptr, C->TU.p);   // W' Cb
+      coldot_rows(st, nb, l, Cb, l, C->TU.p, l, -2.0, C->v5.p);
+    }
+    hmatvec(st, l, 1.0, C->H0.p, p, mu, C->v5.p, Hp);
+    return;
+  }
   const double* Ca = Cb + (size_t)nb * l;
   if (na == 0) {
     fill(st, l, 0.0, C->v5.p);
@@ -513,6 +538,8 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
   // Symmetric QMR keeps the direct form phi_star / T / phi.
   const bool eigcg = C->opt.schur_solver != 1;
   const int nb = e.nb, na = l - nb;
+  const bool comp = eigcg && complement_form(e, l);
+  const int crow = comp ? nb : na;   // rows carried for T[Phi*(x)] (see schur_eig)
   double* sc = C->scal.p;
   double* Wx = C->Wx.p;
   if (eigcg) {
@@ -522,10 +549,14 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
     gemm_acc(st, oz, false, false, l, l, l, 1.0, C->TU.p, l, e.P.p, l, nullptr, 0.0, C->TV.p, l, G_SYM);
     rhs_weights(st, l, nb, e.sig.p, mu, C->TV.p, C->A2.p);
     gemm_acc(st, oz, false, false, l, l, l, 1.0, C->A2.p, l, C->Cb.p, l, nullptr, 0.0, C->TW.p, l, 0);
-    coldot_rows(st, l, l, C->Cb.p, l, C->TW.p, l, 1.0, C->v1.p);
-    axpby(st, l, -1.0, r.r1.p, 1.0, C->v1.p, a1);
-    if (cg_tol_abs <= 0)
+    coldot_rows(st, l, l, C->Cb.p, l, C->TW.p, l, 1.0, C->phia2.p);   // Phi(at2)
+    axpby(st, l, -1.0, r.r1.p, 1.0, C->phia2.p, a1);
+    if (comp) {
+      axpby(st, L2, 1.0 / (2.0 * C->lambda2), C->Q.p, 1.0 / mu, C->KK.p, C->H0.p);
+      if (cg_tol_abs <= 0) sumsq_f64(st, L2, C->A2.p, sc + 11, C->partial.p);   // ||A2||^2
+    } else if (cg_tol_abs <= 0) {
       eig_norms(st, 0, nullptr, nb, nb, l, 0, C->A2.p, nullptr, nullptr, sc + 10, C->partial.p);
+    }
   } else {
     C->force64 = true;
     t_apply(C, e, mu, r.r2.p, rT);
@@ -539,7 +570,7 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
     if (phase == 1) C->force64 = true;   // always verify a tensor-core direction in FP64
     if (phase == 0) {
       fill(st, l, 0.0, dgam);
-      if (eigcg) fill(st, (size_t)na * l, 0.0, Wx);
+      if (eigcg) fill(st, (size_t)crow * l, 0.0, Wx);
       else fill(st, L2, 0.0, TPx);
       KOT_CUDA(cudaMemcpyAsync(ev, a1, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
     } else {
@@ -569,6 +600,9 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
       while (true) {
         // stop test at the current iterate: ||e|| vs tau min(1, kappa ||r|| ||dw||)
         if (cg_tol_abs > 0) sumsq_f64(st, l, dgam, sc + 1, C->partial.p);
+        else if (comp)
+          eig_norms_comp(st, l, dgam, nb, e.sig.p, mu, C->A2.p, Wx, C->KK.p, C->phia2.p, sc + 11, sc + 1,
+                         C->partial.p);
         else eig_norms(st, l, dgam, na, l, l, nb, C->A2.p + (size_t)nb * l, Wx, sc + 11, sc + 1, C->partial.p);
         fetch(C, 8);
         const double ee = C->hs[5 + cur];
@@ -590,11 +624,16 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
         }
         if (stop || it >= cap) break;
         // Hp = Q p/(2 lambda2) + mu p + Phi(T[Phi*(p)]); M5 = alpha rows of T[Phi*(p)] (eigenbasis)
-        schur_eig(C, e, mu, pv, C->M5.p, C->M6.p, Hp);
+        {
+          const double L = l, a = std::min(na, nb);
+          ProfScope ps(st, KC_MATVEC, 4.0 / 3.0 * L * L * L + 8.0 * a * L * L + 2.0 * L * L,
+                       8.0 * (2.0 * L * L + 4.0 * a * L), 4.0 * a * L * L + 2.0 * L * L);
+          schur_eig(C, e, mu, pv, C->M5.p, C->M6.p, Hp);
+        }
         // a = ||e||^2 / p^T H p: x += a p, e -= a H p, p = e + b p (one block, scalars on the
         // device), then T[Phi*(x)] += a T[Phi*(p)]
         cg_step(st, l, Hp, pv, dgam, ev, sc, cur);
-        axpy_ratio(st, (size_t)na * l, sc + 5 + cur, sc + 3, 1.0, C->M5.p, Wx, nullptr);
+        axpy_ratio(st, (size_t)crow * l, sc + 5 + cur, sc + 3, 1.0, C->M5.p, Wx, nullptr);
         cur ^= 1;
         ++it;
       }
@@ -606,8 +645,14 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
   C->last_dir_kind = refine ? (refined_steps == 0 ? 1 : 2) : 0;
   C->force64 = false;
   if (eigcg) {
-    // dX = at2 - T[Phi*(x)] = P D P^T, D = A2 - P^T T[Phi*(x)] P (FP64-accuracy products)
-    assemble_dir(st, l, nb, C->A2.p, Wx, C->TG.p);
+    // dX = at2 - T[Phi*(x)] = P D P^T, D = A2 - P^T T[Phi*(x)] P (FP64-accuracy products); the
+    // complement form carries no alpha rows, so D = A2 - Psi o Vx from Vx = Cb diag(x) Cb^T
+    if (comp) {
+      gemm_acc(st, ozp(C), false, true, l, l, l, 1.0, C->Cb.p, l, C->Cb.p, l, dgam, 0.0, C->TV.p, l, G_SYM);
+      assemble_psi(st, l, nb, e.sig.p, mu, C->A2.p, C->TV.p, C->TG.p);
+    } else {
+      assemble_dir(st, l, nb, C->A2.p, Wx, C->TG.p);
+    }
     gemm_acc(st, ozp(C), false, true, l, l, l, 1.0, C->TG.p, l, e.P.p, l, nullptr, 0.0, C->TW.p, l, 0);
     gemm_acc(st, ozp(C), false, false, l, l, l, 1.0, e.P.p, l, C->TW.p, l, nullptr, 0.0, dX, l, G_SYM);
   } else {
@@ -689,6 +734,7 @@ void compute_eg_L(kot_ctx* C) {
   gemm_acc(C->st, ozp(C), true, false, l, l, l, 1.0, C->R.p, l, C->R.p, l, nullptr, 0.0, C->M1.p, l,
            G_KHI_ROW | G_KHI_COL | G_SYM);
   rowsum_bounds(C->st, l, C->Q.p, C->M1.p, C->bounds.p);
+  square_elems(C->st, (size_t)l * l, C->M1.p, C->KK.p);   // Kt o Kt (complement form of CG)
   KOT_CUDA(cudaMemcpyAsync(C->hs, C->bounds.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, C->st));
   KOT_CUDA(cudaStreamSynchronize(C->st));
   C->eg_L = C->hs[0] / (2 * C->lambda2) + std::sqrt(C->hs[1]);
@@ -768,7 +814,7 @@ kot_status kot_create(kot_ctx** out, const kot_options* opt) {
       !(o.alpha1 > 0) || !(o.alpha2 >= o.alpha1) || !(o.beta0 > 0) || !(o.beta1 > 0) ||
       !(o.beta2 > 0) || !(o.theta0 > 0) || !(o.theta_min > 0) || !(o.theta_max >= o.theta_min) ||
       !(o.jitter >= 0) || !(o.jitter_max >= o.jitter) || o.eig_ctas < 0 || !(o.mixed_switch >= 0) || o.batch_workers < 0 || o.eig_refine < 0 ||
-      (o.schur_solver != 0 && o.schur_solver != 1) ||
+      (o.schur_solver != 0 && o.schur_solver != 1) || (o.gram_fp32 != 0 && o.gram_fp32 != 1) ||
       (o.precision != KOT_FP64 && o.precision != KOT_MIXED))
     return KOT_ERR_INVALID;
   int ndev = 0;
@@ -804,7 +850,7 @@ kot_status kot_destroy(kot_ctx* C) {
   for (DevBuf<double>* b : {&C->Q, &C->K, &C->R, &C->z, &C->w_mu, &C->w_nu, &C->c, &C->g, &C->X,
                             &C->vg, &C->vX, &C->tg, &C->tX, &C->dg, &C->dX, &C->M1, &C->M2,
                             &C->M3, &C->M4, &C->M5, &C->M6, &C->TU, &C->TV, &C->TW, &C->TG,
-                            &C->Cb, &C->A2, &C->Wx,
+                            &C->Cb, &C->A2, &C->Wx, &C->KK, &C->H0, &C->phia2,
                             &C->v1, &C->v2, &C->v3, &C->v4, &C->v5, &C->v6, &C->w1, &C->w2,
                             &C->w3, &C->partial,
                             &C->scal, &C->bounds, &C->rw.r1, &C->rw.r2, &C->rv.r1, &C->rv.r2,
@@ -861,7 +907,8 @@ kot_status kot_build_features(kot_ctx* C, int d, int n, const double* X, const d
     C->stage[7].alloc(pb);
     pair_mean_f64(st, n, d, dX, inv2s2, C->scal.p + 10, C->stage[7].p, pb);
     pair_mean_f64(st, n, d, dY, inv2s2, C->scal.p + 11, C->stage[7].p, pb);
-    gram_f64(st, l, d, dXf, dYf, inv2s2, lambda2, C->w_mu.p, C->w_nu.p, C->Q.p, C->K.p, C->c.p, C->z.p);
+    gram_f64(st, l, d, dXf, dYf, inv2s2, lambda2, C->w_mu.p, C->w_nu.p, C->Q.p, C->K.p, C->c.p, C->z.p,
+             C->opt.gram_fp32 != 0);
     KOT_CUDA(cudaMemcpyAsync(C->hs + 10, C->scal.p + 10, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     KOT_CUDA(cudaStreamSynchronize(st));
     C->q2 = C->hs[10] + C->hs[11];
@@ -1460,6 +1507,7 @@ kot_status kot_profile_read(kot_ctx* C, int cls, kot_kernel_stats* out) {
     out->ms = C->prof.ms[cls];
     out->flops = C->prof.flops[cls];
     out->bytes = C->prof.bytes[cls];
+    out->exec_flops = C->prof.exec[cls];
   });
 }
 
@@ -1477,6 +1525,59 @@ kot_status kot_get_history(kot_ctx* C, double* hist, int cap, int* count) {
   std::copy(C->hist.begin(), C->hist.begin() + m, hist);
   *count = m;
   return KOT_OK;
+}
+
+kot_status kot_bootstrap_solve(kot_ctx* C, int B, int n, const double* Xs, const double* Ys, double tol,
+                               double* gamma_out, kot_result* res) {
+  if (!C) return KOT_ERR_INVALID;
+  if (B < 0 || n < 1 || (B > 0 && (!Xs || !Ys || !gamma_out || !res)) || !pos_finite(tol)) {
+    C->err = "kot_bootstrap_solve: invalid argument";
+    return KOT_ERR_INVALID;
+  }
+  if (!C->have || !C->have_samples) {
+    C->err = "kot_bootstrap_solve: needs the filling points of kot_build_features";
+    return KOT_ERR_STATE;
+  }
+  kot_status first = KOT_OK;
+  const int d = C->d, l = C->l;
+  for (int b = 0; b < B; ++b) {
+    // the resample's sample terms of the dual problem (Sec. 3): w_mu, w_nu, q2 and z; Q, K, R,
+    // the jitter and the EG step bound depend on the filling points only and are kept
+    kot_status s = run(C, [&] {
+      KOT_CUDA(cudaSetDevice(C->opt.device));
+      cudaStream_t st = C->st;
+      const size_t nd = (size_t)n * d;
+      const double* dX = dev_in(C, 0, Xs + (size_t)b * nd, nd);
+      const double* dY = dev_in(C, 1, Ys + (size_t)b * nd, nd);
+      const double inv2s2 = 1.0 / (2.0 * C->sigma * C->sigma);
+      embed_f64(st, n, d, l, dX, C->sXf.p, inv2s2, C->w_mu.p);
+      embed_f64(st, n, d, l, dY, C->sYf.p, inv2s2, C->w_nu.p);
+      const int pb = pair_blocks(n);
+      C->stage[7].alloc(pb);
+      pair_mean_f64(st, n, d, dX, inv2s2, C->scal.p + 10, C->stage[7].p, pb);
+      pair_mean_f64(st, n, d, dY, inv2s2, C->scal.p + 11, C->stage[7].p, pb);
+      cost_z_f64(st, l, d, C->sXf.p, C->sYf.p, C->lambda2, C->w_mu.p, C->w_nu.p, C->c.p, C->z.p);
+      // the samples the potentials use are the resample's
+      C->sX.alloc(nd);
+      C->sY.alloc(nd);
+      KOT_CUDA(cudaMemcpyAsync(C->sX.p, dX, nd * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      KOT_CUDA(cudaMemcpyAsync(C->sY.p, dY, nd * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      KOT_CUDA(cudaMemcpyAsync(C->hs + 10, C->scal.p + 10, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      KOT_CUDA(cudaStreamSynchronize(st));
+      C->q2 = C->hs[10] + C->hs[11];
+      C->n = n;
+    });
+    if (s != KOT_OK) {   // the resample's features failed: report it for this and the rest
+      for (int r = b; r < B; ++r) {
+        res[r] = kot_result{};
+        res[r].status = s;
+      }
+      return first == KOT_OK ? s : first;
+    }
+    s = kot_ssn_solve(C, tol, gamma_out + (size_t)b * l, nullptr, nullptr, nullptr, &res[b]);
+    if (first == KOT_OK && s != KOT_OK) first = s;
+  }
+  return first;
 }
 
 kot_status kot_batch_solve(kot_ctx* C, int B, const kot_problem* probs, kot_result* res) {

@@ -84,27 +84,29 @@ enum KClass : int {
                         // counted as gemm_f64 or gemm_oz)
   KC_GEMM_OZ = 9,       // k_oz_gemm (FP64-accurate products emulated on the tensor cores)
   KC_OZ_AUX = 10,       // slicing (k_oz_split_cluster, or k_oz_rowexp + k_oz_split) and k_oz_finalize
-  KC_COUNT = 11
+  KC_MATVEC = 11,       // one Schur-operator application of CG (all its launches, Algorithm 1)
+  KC_COUNT = 12
 };
 
 // When a profiler is installed for the calling thread, instrumented launch sites record a CUDA
 // event pair around each launch of an enabled class together with the launch's algorithmic
-// flop and byte counts; collect() waits for the events and accumulates per class.
+// flop and byte counts and the flops it executes (e.g. an FP64-accurate product of 2MNK flops
+// executes 2MNK per BF16 slice pair); collect() waits for the events and accumulates per class.
 struct Profiler {
   int mask = 0;
   int every = 1;                       // time one launch in `every` of each enabled class
   long long seen[KC_COUNT] = {};       // launches of each enabled class since the last reset
-  struct Pending { int cls; cudaEvent_t a, b; double flops, bytes; };
+  struct Pending { int cls; cudaEvent_t a, b; double flops, bytes, exec; };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
   long launches[KC_COUNT] = {};
-  double ms[KC_COUNT] = {}, flops[KC_COUNT] = {}, bytes[KC_COUNT] = {};
+  double ms[KC_COUNT] = {}, flops[KC_COUNT] = {}, bytes[KC_COUNT] = {}, exec[KC_COUNT] = {};
   bool on(int cls) const { return (mask >> cls) & 1; }
   // enabled, and this launch is one of the sampled ones
   bool take(int cls) { return on(cls) && (seen[cls]++ % every) == 0; }
   cudaEvent_t get_event();
   void begin(cudaStream_t st, int cls, cudaEvent_t* a);
-  void end(cudaStream_t st, int cls, cudaEvent_t a, double fl, double by);
+  void end(cudaStream_t st, int cls, cudaEvent_t a, double fl, double by, double ex);
   void collect();
   void reset();
   void release();
@@ -112,19 +114,20 @@ struct Profiler {
 Profiler* current_profiler();
 void set_current_profiler(Profiler* p);
 
-// RAII helper around one launch: `ProfScope ps(st, KC_x, flops, bytes); launch...;`
+// RAII helper around one launch: `ProfScope ps(st, KC_x, flops, bytes[, executed flops]); launch...;`
 struct ProfScope {
   Profiler* p;
   cudaStream_t st;
   int cls;
-  double fl, by;
+  double fl, by, ex;
   cudaEvent_t a = nullptr;
-  ProfScope(cudaStream_t s, int c, double f, double b) : p(current_profiler()), st(s), cls(c), fl(f), by(b) {
+  ProfScope(cudaStream_t s, int c, double f, double b, double e = -1.0)
+      : p(current_profiler()), st(s), cls(c), fl(f), by(b), ex(e < 0.0 ? f : e) {
     if (p && p->take(cls)) p->begin(st, cls, &a);
     else p = nullptr;
   }
   ~ProfScope() {
-    if (p) p->end(st, cls, a, fl, by);
+    if (p) p->end(st, cls, a, fl, by, ex);
   }
 };
 
@@ -193,6 +196,16 @@ void two_norms(cudaStream_t st, size_t n1, const double* x, size_t n2, const dou
 // kReduceBlocks doubles.
 void eig_norms(cudaStream_t st, size_t n1, const double* x, int rows, int cols, int ld, int nb,
                const double* A, const double* W, const double* base, double* out2, double* partial);
+// Complement form of the same test (Sec. 4.3, last paragraph): out2[0] = |x|^2 (l entries),
+// out2[1] = ||A2 - Psi o Vx||_F^2 from the alpha-bar rows U of Vx = Cb diag(x) Cb^T (nb x l, ld l),
+// A2 (l x l), KK = Kt o Kt, phi_at2 = Phi(at2) and *base = ||A2||_F^2 (see k_eig_norms_comp).
+void eig_norms_comp(cudaStream_t st, int l, const double* x, int nb, const double* sig, double mu,
+                    const double* A2, const double* U, const double* KK, const double* phi_at2,
+                    const double* base, double* out2, double* partial);
+// out2 = the column sums of nb (s1, s2) pairs in partial
+void sum_pairs(cudaStream_t st, int nb, const double* partial, double* out2);
+// out[i] = x[i]^2 (out may alias x)
+void square_elems(cudaStream_t st, size_t n, const double* x, double* out);
 // y = alpha A x + mu x + v (v may be null)
 void hmatvec(cudaStream_t st, int n, double alpha, const double* A, const double* x, double mu,
              const double* v, double* y);
@@ -226,9 +239,13 @@ int pair_blocks(int n);                                            // partials t
 void potential_f64(cudaStream_t st, int m, int d, int n, const double* S, int l, const double* Sf,
                    const double* gamma, const double* Pq, double sigma, double lambda2, double* u,
                    double* grad, double* tmap);
+// fp32: the distances and exponentials of Q and K in FP32 (k_gram_f32), else FP64
 void gram_f64(cudaStream_t st, int l, int d, const double* Xf, const double* Yf, double inv2s2,
               double lambda2, const double* w_mu, const double* w_nu, double* Q, double* K,
-              double* c, double* z);
+              double* c, double* z, bool fp32 = false);
+// c_i = ||xf_i - yf_i||^2, z_i = w_mu_i + w_nu_i - lambda2 c_i (the cost and dual vector of Sec. 3)
+void cost_z_f64(cudaStream_t st, int l, int d, const double* Xf, const double* Yf, double lambda2,
+                const double* w_mu, const double* w_nu, double* c, double* z);
 // Upper Cholesky of A + eps I in place (A: l x l, only the upper triangle is read).  The lower
 // triangle is zeroed.  *info (device int) = 0 on success, j+1 if pivot j was not positive.
 void zero_lower(cudaStream_t st, int l, double* A);        // A[i][j] = 0 for j < i
@@ -349,10 +366,14 @@ void gemm_acc(cudaStream_t st, OzWork* oz, bool ta, bool tb, int M, int N, int K
               double* C, int ldc, int flags);
 
 // ------------------------------------------------------------------ Newton pieces (newton.cu)
-// Scale rows of V (na x l) for the G + G^T form of T: columns in alpha by 1/(2 mu), columns in
-// alpha-bar by xi (or the complement weights).  See t_apply in kot_api.cu.
+// V = weights o U for the rows of the G + G^T form of T (|alpha| rows: columns in alpha by 1/(2 mu),
+// columns in alpha-bar by xi) or of the complement form (|alpha-bar| rows: 1/(2 mu) on alpha-bar,
+// 1/mu - xi on alpha).  U null: in place on V.  See t_apply and schur_eig in kot_api.cu.
 void t_weights(cudaStream_t st, int l, int nb, const double* sig, double mu, int complement,
-               double* V);
+               double* V, const double* U = nullptr);
+// D = A2 - Psi o Vx (l x l): the eigenbasis form of dX = at2 - T[Phi*(x)] from the full Vx.
+void assemble_psi(cudaStream_t st, int l, int nb, const double* sig, double mu, const double* A2,
+                  const double* Vx, double* D);
 // Right-hand side of Algorithm 1 in the eigenbasis: A2 = -(1 + Psi) o B/(mu + 1) for B = P^T r2 P
 // (l x l), i.e. A2 = P^T at2 P.
 void rhs_weights(cudaStream_t st, int l, int nb, const double* sig, double mu, const double* B, double* A2);

@@ -8,31 +8,105 @@ namespace {
 
 inline int cdiv(size_t a, int b) { return (int)((a + b - 1) / b); }
 
+__device__ double block_sum256(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
 // xi_ij = eta_ij / (mu + 1 - eta_ij), eta_ij = sig_i / (sig_i - sig_j), i in alpha, j in alpha-bar
 __device__ __forceinline__ double xi_of(double si, double sj, double mu) {
   const double eta = si / (si - sj);
   return eta / (mu + 1.0 - eta);
 }
 
-// V: rows x l.  G + G^T form (complement = 0): row r is eigen-index nb + r (in alpha); column j in
-// alpha (j >= nb) is scaled by 1/(2 mu), column j in alpha-bar by xi(sig_{nb+r}, sig_j).
-// Complement form (complement = 1): row r is eigen-index r (in alpha-bar); column j in alpha-bar
-// is scaled by 1/(2 mu), column j in alpha by 1/mu - xi(sig_j, sig_r).
+// Weight of entry (r, j) of the carried rows.  G + G^T form (complement = 0): row r is
+// eigen-index nb + r (in alpha); column j in alpha (j >= nb) is weighted 1/(2 mu), column j in
+// alpha-bar xi(sig_{nb+r}, sig_j).  Complement form (complement = 1; Psi' = E/mu - Psi): row r is
+// eigen-index r (in alpha-bar); column j in alpha-bar is weighted 1/(2 mu), column j in alpha
+// 1/mu - xi(sig_j, sig_r).
+__device__ __forceinline__ double t_weight(int r, int j, int nb, const double* __restrict__ sig, double mu,
+                                           int complement) {
+  if (!complement) return (j >= nb) ? 0.5 / mu : xi_of(sig[nb + r], sig[j], mu);
+  return (j < nb) ? 0.5 / mu : (1.0 / mu - xi_of(sig[j], sig[r], mu));
+}
+
+// V = weights o U over rows x l (V may alias U).
 __global__ void k_t_weights(int rows, int l, int nb, const double* __restrict__ sig, double mu,
-                            int complement, double* __restrict__ V) {
+                            int complement, const double* U, double* V) {
   pdl_wait();
   pdl_trigger();
   const int j = blockIdx.x * 32 + threadIdx.x, r = blockIdx.y * 8 + threadIdx.y;
   if (r >= rows || j >= l) return;
-  double w;
-  if (!complement) {
-    const int i = nb + r;
-    w = (j >= nb) ? 0.5 / mu : xi_of(sig[i], sig[j], mu);
-  } else {
-    const int i = r;
-    w = (j < nb) ? 0.5 / mu : (1.0 / mu - xi_of(sig[j], sig[i], mu));
+  const size_t o = (size_t)r * l + j;
+  V[o] = U[o] * t_weight(r, j, nb, sig, mu, complement);
+}
+
+// Norms of the CG stopping test in the eigenbasis, complement form (Sec. 4.3, last paragraph):
+// with U the alpha-bar rows of Vx = Cb diag(x) Cb^T and W' = weights o U (complement weights),
+//   out[1] = ||A2||^2 + sum_{r < nb, j} (4 A2_rj W'_rj + w'_j W'_rj^2 - (4/mu) W'_rj U_rj)
+//            - (2/mu) x . Phi(at2) + x^T (Kt o Kt) x / mu^2,   w'_j = 4 (j < nb), 2 (j >= nb),
+// which is ||A2 - Psi o Vx||_F^2 = ||at2 - T[Phi*(x)]||_F^2 for orthogonal P; out[0] = |x|^2.
+// *base = ||A2||_F^2.  One block writes out directly; several write partial pairs.
+__global__ void k_eig_norms_comp(int l, const double* __restrict__ x, int nb, const double* __restrict__ sig,
+                                 double mu, const double* __restrict__ A2, const double* __restrict__ U,
+                                 const double* __restrict__ KK, const double* __restrict__ phi_at2,
+                                 const double* __restrict__ base, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ double sh[256];
+  double s1 = 0.0, s2 = 0.0, s3 = 0.0;   // |x|^2; the alpha-bar row terms; x^T KK x - 2 mu x.phi
+  const size_t stride = (size_t)gridDim.x * 256;
+  const size_t t0 = blockIdx.x * 256 + threadIdx.x;
+  for (size_t i = t0; i < (size_t)l; i += stride) {
+    s1 = fma(x[i], x[i], s1);
+    s3 = fma(-2.0 * mu * x[i], phi_at2[i], s3);
   }
-  V[(size_t)r * l + j] *= w;
+  const size_t nr = (size_t)nb * l;
+  for (size_t i = t0; i < nr; i += stride) {
+    const int r = (int)(i / l), j = (int)(i - (size_t)r * l);
+    const double u = U[i], w = u * t_weight(r, j, nb, sig, mu, 1);
+    const double a = A2[i];   // rows r < nb of A2 (ld l) are entries i
+    s2 += 4.0 * a * w + (j < nb ? 4.0 : 2.0) * w * w - (4.0 / mu) * w * u;
+  }
+  const size_t n2 = (size_t)l * l;
+  for (size_t i = t0; i < n2; i += stride) {
+    const int r = (int)(i / l), j = (int)(i - (size_t)r * l);
+    s3 = fma(x[r] * KK[i], x[j], s3);
+  }
+  s2 += s3 / (mu * mu);
+  if (base && blockIdx.x == 0 && threadIdx.x == 0) s2 += *base;
+  s1 = block_sum256(s1, sh);
+  __syncthreads();
+  s2 = block_sum256(s2, sh);
+  if (threadIdx.x == 0) {
+    out[2 * blockIdx.x] = s1;
+    out[2 * blockIdx.x + 1] = s2;
+  }
+}
+
+// D = A2 - Psi o Vx over l x l (Psi of Sec. 4.3: 1/mu on alpha x alpha, xi on alpha x alpha-bar and
+// its transpose, 0 on alpha-bar x alpha-bar): the eigenbasis form of dX = at2 - T[Phi*(x)].
+__global__ void k_assemble_psi(int l, int nb, const double* __restrict__ sig, double mu,
+                               const double* __restrict__ A2, const double* __restrict__ Vx,
+                               double* __restrict__ D) {
+  pdl_wait();
+  pdl_trigger();
+  const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
+  if (i >= l || j >= l) return;
+  const bool ai = i >= nb, aj = j >= nb;
+  double psi = 0.0;
+  if (ai && aj) psi = 1.0 / mu;
+  else if (ai) psi = xi_of(sig[i], sig[j], mu);
+  else if (aj) psi = xi_of(sig[j], sig[i], mu);
+  const size_t o = (size_t)i * l + j;
+  D[o] = A2[o] - psi * Vx[o];
 }
 
 // A2 = -(1 + Psi) o B / (mu + 1) over l x l (Psi of Sec. 4.3: 1/mu on alpha x alpha, xi on
@@ -87,11 +161,33 @@ __global__ void k_count_nonpos(int l, const double* __restrict__ sig, int* __res
 }  // namespace
 
 void t_weights(cudaStream_t st, int l, int nb, const double* sig, double mu, int complement,
-               double* V) {
+               double* V, const double* U) {
   const int rows = complement ? nb : l - nb;
   if (rows <= 0) return;
   launch_pdl(k_t_weights, dim3(cdiv(l, 32), cdiv(rows, 8)), dim3(32, 8), 0, st, rows, l, nb, sig, mu,
-             complement, V);
+             complement, U ? U : (const double*)V, V);
+  KOT_CHECK_LAUNCH();
+}
+
+void eig_norms_comp(cudaStream_t st, int l, const double* x, int nb, const double* sig, double mu,
+                    const double* A2, const double* U, const double* KK, const double* phi_at2,
+                    const double* base, double* out2, double* partial) {
+  const size_t n = (size_t)l * l;
+  if (n <= 4096) {
+    launch_pdl(k_eig_norms_comp, dim3(1), dim3(256), 0, st, l, x, nb, sig, mu, A2, U, KK, phi_at2, base, out2);
+    KOT_CHECK_LAUNCH();
+    return;
+  }
+  const int nbk = kReduceBlocks / 2;   // partial holds kReduceBlocks doubles: nbk pairs
+  launch_pdl(k_eig_norms_comp, dim3(nbk), dim3(256), 0, st, l, x, nb, sig, mu, A2, U, KK, phi_at2, base,
+             partial);
+  sum_pairs(st, nbk, partial, out2);
+  KOT_LAUNCHED(1);
+}
+
+void assemble_psi(cudaStream_t st, int l, int nb, const double* sig, double mu, const double* A2,
+                  const double* Vx, double* D) {
+  launch_pdl(k_assemble_psi, dim3(cdiv(l, 32), cdiv(l, 8)), dim3(32, 8), 0, st, l, nb, sig, mu, A2, Vx, D);
   KOT_CHECK_LAUNCH();
 }
 

@@ -34,7 +34,8 @@ class Options(C.Structure):
                 ("theta_max", C.c_double), ("eg_step", C.c_double), ("jitter", C.c_double),
                 ("jitter_max", C.c_double), ("use_eg", C.c_int), ("record_history", C.c_int),
                 ("eig_ctas", C.c_int), ("mixed_switch", C.c_double),
-                ("batch_workers", C.c_int), ("eig_refine", C.c_int), ("schur_solver", C.c_int)]
+                ("batch_workers", C.c_int), ("eig_refine", C.c_int), ("schur_solver", C.c_int),
+                ("gram_fp32", C.c_int)]
 
 
 class Result(C.Structure):
@@ -61,15 +62,16 @@ EXPORTS = ["kot_default_options", "kot_create", "kot_destroy", "kot_last_error",
            "kot_newton_direction", "kot_ssn_solve", "kot_get_history", "kot_batch_solve",
            "kot_profile", "kot_profile_read", "kot_launch_count",
            "kot_embedding_sqnorm_noalloc", "kot_dense_product", "kot_get_trace", "kot_eig_sym",
-           "kot_eg_solve", "kot_potentials", "kot_profile_every", "kot_autotune", "kot_wait_probe"]
+           "kot_eg_solve", "kot_potentials", "kot_profile_every", "kot_autotune", "kot_wait_probe",
+           "kot_bootstrap_solve"]
 
 KERNEL_CLASSES = ["gemm_f64", "jacobi_f64", "reserved", "embed", "pair_sums", "gram",
-                  "cholesky", "gemm_tc", "eig_refine", "gemm_oz", "oz_aux"]
+                  "cholesky", "gemm_tc", "eig_refine", "gemm_oz", "oz_aux", "schur_matvec"]
 
 
 class KernelStats(C.Structure):
     _fields_ = [("launches", C.c_longlong), ("ms", C.c_double), ("flops", C.c_double),
-                ("bytes", C.c_double)]
+                ("bytes", C.c_double), ("exec_flops", C.c_double)]
 
 _lib = None
 
@@ -96,6 +98,7 @@ def lib() -> C.CDLL:
         "kot_ssn_solve": (i, [vp, d, vp, vp, vp, vp, C.POINTER(Result)]),
         "kot_get_history": (i, [vp, vp, i, C.POINTER(i)]),
         "kot_batch_solve": (i, [vp, i, C.POINTER(Problem), C.POINTER(Result)]),
+        "kot_bootstrap_solve": (i, [vp, i, i, vp, vp, d, vp, C.POINTER(Result)]),
         "kot_profile": (i, [vp, i]),
         "kot_profile_every": (i, [vp, i]),
         "kot_autotune": (i, [vp, i, vp]),
@@ -287,6 +290,16 @@ class Context:
         cnt = C.c_int(0)
         self._check(lib().kot_get_history(self.h, buf.ctypes.data, cap, C.byref(cnt)))
         return buf[:cnt.value].copy()
+
+    def bootstrap_solve(self, Xs, Ys, tol, gammas, allow_no_convergence=True):
+        """Resamples Xs, Ys (B x n x d) sharing the filling points of the last build_features;
+        gammas: B x l output.  Returns the B results."""
+        B, n = Xs.shape[0], Xs.shape[1]
+        res = (Result * B)()
+        s = lib().kot_bootstrap_solve(self.h, B, n, _ptr(Xs), _ptr(Ys), tol, _ptr(gammas), res)
+        ok = (OK, ERR_NO_CONVERGENCE) if allow_no_convergence else (OK,)
+        self._check(s, ok)
+        return list(res)
 
     def batch_solve(self, problems, gammas, allow_no_convergence=True):
         """problems: list of objects with X, Y, Xf, Yf (arrays), sigma, lambda1, lambda2, tol."""

@@ -207,3 +207,28 @@ def by_name(name: str) -> Problem:
         "d64_n4000_l2048": feature_like,
     }
     return table[name]()
+
+
+def bootstrap_resamples(p: Problem, count: int, seed: int):
+    """`count` bootstrap resamples of the samples of p, drawn with replacement (X and Y
+    independently, each of size n), the filling points kept: the bootstrap setting in which Q, K
+    and R are shared.  Returns (Xs, Ys), each count x n x d."""
+    rng = np.random.default_rng(seed)
+    n = p.n
+    ix = rng.integers(0, n, size=(count, n))
+    iy = rng.integers(0, n, size=(count, n))
+    return np.ascontiguousarray(p.X[ix]), np.ascontiguousarray(p.Y[iy])
+
+
+def clustered_symmetric(l: int, seed: int, clusters: int = 6, width: float = 1e-9) -> np.ndarray:
+    """Symmetric l x l matrix whose eigenvalues sit half in a few tight clusters of both signs
+    (width `width`) and half spread over [-1, 1], in a random orthogonal basis: the kind of
+    spectrum the matrices Z = X - Phi*(gamma) - lambda1 I of an SSN solve have (many gaps below
+    1e-6 ||Z||, eigenvalues on both sides of zero)."""
+    rng = np.random.default_rng(seed)
+    centers = rng.uniform(-1.0, 1.0, clusters)
+    lam = np.where(rng.random(l) < 0.5, centers[rng.integers(0, clusters, l)]
+                   + width * rng.standard_normal(l), rng.uniform(-1.0, 1.0, l))
+    Qm, _ = np.linalg.qr(rng.standard_normal((l, l)))
+    Z = (Qm * lam) @ Qm.T
+    return 0.5 * (Z + Z.T)

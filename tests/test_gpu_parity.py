@@ -93,15 +93,18 @@ def test_residual_matches_oracle(name, scale):
     assert n[2] == pytest.approx(ref.norm, rel=1e-10)
 
 
-@pytest.mark.parametrize("name,scale,mu", [("paper_d2_l50", 0.05, 0.3), ("paper_d2_l50", 3.0, 0.3),
-                                           ("paper_d5_l97", 0.02, 1e-2), ("paper_d5_l97", 2.0, 1.0)])
-def test_newton_direction_matches_oracle(name, scale, mu):
+# (|alpha|, |alpha-bar|) of the points: 20/30 and 25/25 take the G + G^T form of T in CG, 44/6,
+# 50/47 and 87/10 its complement form (Sec. 4.3, last paragraph)
+@pytest.mark.parametrize("name,scale,mu,na_expect", [
+    ("paper_d2_l50", 0.001, 0.3, 20), ("paper_d2_l50", 0.05, 0.3, 25), ("paper_d2_l50", 3.0, 0.3, 44),
+    ("paper_d5_l97", 0.02, 1e-2, 50), ("paper_d5_l97", 2.0, 1.0, 87)])
+def test_newton_direction_matches_oracle(name, scale, mu, na_expect):
     p = WORKLOADS[name]()
     F, ctx = _features(p)
     g, X = _point(F, 11, scale)
     res = ko.residual(F, g, X)
     na = int(res.eig.alpha.sum())
-    assert 0 < na < F.l        # both the alpha and alpha-bar blocks are exercised
+    assert na == na_expect and 0 < na < F.l   # both the alpha and alpha-bar blocks are exercised
     l = F.l
     dg, dX = Z(l), Z(l, l)
     # nearly exact direction: compare to the oracle's CG run to the same absolute tolerance
@@ -629,3 +632,55 @@ def test_newton_direction_is_exactly_symmetric(precision):
         dg, dX = Z(p.l), Z(p.l, p.l)
         ctx.newton_direction(T(g), T(X), mu, dg, dX)
         assert torch.equal(dX, dX.T), mu
+
+
+@pytest.mark.parametrize("precision,obj_rel", [(kot.FP64, 1e-8), (kot.MIXED, 1e-6)])
+def test_bootstrap_solve_shares_R_and_matches_oracle(precision, obj_rel):
+    # bootstrap resamples with the filling points kept (Sec. 5 setting): K and R are built once;
+    # every resample's solve must match the oracle's solve of that resample's own features
+    p = WORKLOADS["paper_d5_l97"]()
+    Xs, Ys = wl.bootstrap_resamples(p, 3, seed=17)
+    ctx = kot.Context(device=0, precision=precision)
+    ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
+    R0, Q0 = Z(p.l, p.l), Z(p.l, p.l)
+    ctx.get_features(Q=Q0, R=R0)
+    G = Z(3, p.l)
+    res = ctx.bootstrap_solve(T(Xs), T(Ys), p.tol, G)
+    R1, Q1, z1, q2 = Z(p.l, p.l), Z(p.l, p.l), Z(p.l), Z(1)
+    ctx.get_features(Q=Q1, R=R1, z=z1, q2=q2)
+    assert torch.equal(R0, R1) and torch.equal(Q0, Q1)
+    for b in range(3):
+        F = ko.build_features(Xs[b], Ys[b], p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
+        np.testing.assert_allclose(F.R, N(R1), atol=1e-12)           # the same factor for all
+        ref = ko.ssn_solve(F, p.tol)
+        r = res[b]
+        assert r.status == kot.OK and ref.converged, (b, r.iters, ref.iters)
+        assert abs(r.iters - ref.iters) <= 3, (b, r.iters, ref.iters)
+        assert r.objective == pytest.approx(ref.objective, rel=obj_rel), b
+        assert np.abs(N(G[b]) - ref.gamma).max() <= 1e-5 * np.abs(ref.gamma).max(), b
+        if b == 2:   # the context holds the last resample's problem data
+            np.testing.assert_allclose(N(z1), F.z, rtol=1e-12, atol=1e-14)
+            assert N(q2)[0] == pytest.approx(F.q2, rel=1e-12)
+
+
+@pytest.mark.parametrize("precision", [kot.FP64, kot.MIXED])
+def test_fp32_gram_option(precision):
+    # Q and K from FP32 distances and exponentials (the FP32 Gram of the large-l configuration):
+    # entries within FP32 rounding of the oracle's FP64 ones, and the solve within the mixed-form
+    # gates of the FP64 oracle (relative 1e-6 on f(gamma), 1e-5 on gamma)
+    p = WORKLOADS["paper_d5_l97"]()
+    F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
+    ctx = kot.Context(device=0, precision=precision, gram_fp32=1)
+    ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
+    l = p.l
+    Q, K = Z(l, l), Z(l, l)
+    ctx.get_features(Q=Q, K=K)
+    np.testing.assert_allclose(N(Q), F.Q, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(N(K), F.K, rtol=1e-5, atol=1e-6)
+    assert torch.equal(Q, Q.T) and torch.equal(K, K.T)
+    ref = ko.ssn_solve(F, p.tol)
+    g = Z(l)
+    res = ctx.ssn_solve(p.tol, g)
+    assert res.status == kot.OK and ref.converged
+    assert res.objective == pytest.approx(ref.objective, rel=1e-6)
+    assert np.abs(N(g) - ref.gamma).max() <= 1e-5 * np.abs(ref.gamma).max()
