@@ -242,6 +242,8 @@ def main():
     ap.add_argument("--slices", type=int, default=6, help="slices of the emulated product (--method product)")
     ap.add_argument("--sizes", default="64,160,300,512,1024,2048", help="sizes l (--method eig)")
     ap.add_argument("--gram-fp32", action="store_true", help="Gram matrices in FP32 (--method features)")
+    ap.add_argument("--no-large-l", action="store_true",
+                    help="skip the fixed-iteration lines at C3's and C5's shapes (--method ssn)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -356,6 +358,11 @@ def main():
         finals["mixed" if prec == kot.MIXED else "fp64"] = (g0.cpu().numpy(), X0.cpu().numpy(), r0)
         c.close()
 
+    # ---- untimed by the step events: fixed-iteration solves at the large-l shapes
+    large = None
+    if not args.no_large_l and world == 1 and args.workload == "paper_d5_n1000_l300":
+        large = large_l_lines(main_prec, dev, local_rank)
+
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
     if not args.skip_e2e:
@@ -363,7 +370,7 @@ def main():
     if rank == 0:
         report(args, probs, world, ms_max, ms_local, stats, launches, iters, conv, clocks, peaks,
                None if args.skip_other else (other_prec, o_value, o_ms_max, o_iters, o_conv), e2e,
-               conv_all, tuned, finals)
+               conv_all, tuned, finals, large)
     if world > 1:
         dist.destroy_process_group()
 
@@ -741,8 +748,48 @@ def errors_vs_oracle(F, ref, finals):
     return out
 
 
+# Large-l shapes in the Sec. 5 regime: Algorithm 2 does not reach 1e-6 there within 200 iterations,
+# so each is timed over a fixed number of iterations (one warm-up solve first).
+LARGE_L = [("paper_d10_n2000_l1024", 12), ("paper_d64_n4000_l2048", 5)]
+
+
+def large_l_lines(prec, dev, local_rank):
+    """Per-iteration time of Algorithm 2 at C3's (l = 1024) and C5's (l = 2048) shapes over a fixed
+    number of iterations, with the feature assembly timed separately (CUDA events)."""
+    import torch
+    from paper_2310_14087_gb300 import kot
+    out = {}
+    stream = torch.cuda.Stream(device=dev)
+    for name, k in LARGE_L:
+        ctx = kot.Context(device=local_rank, stream=stream.cuda_stream, precision=prec, max_iter=k)
+        p = make_problem(name, 0, 0)
+        dp = kot.DeviceProblem.from_problem(p, dev)
+        g = torch.zeros(p.l, dtype=torch.float64, device=dev)
+        build = lambda: ctx.build_features(dp.X, dp.Y, dp.Xf, dp.Yf, dp.sigma, dp.lambda1, dp.lambda2)
+        build()
+        ctx.ssn_solve(p.tol, g, allow_no_convergence=True)          # warm-up (allocations)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+        build()
+        with torch.cuda.stream(stream):
+            ev[1].record(stream)
+        r = ctx.ssn_solve(p.tol, g, allow_no_convergence=True)
+        with torch.cuda.stream(stream):
+            ev[2].record(stream)
+        ev[2].synchronize()
+        solve_ms = ev[1].elapsed_time(ev[2])
+        out[name] = {**config_of(name), "iterations": r.iters, "residual_after": r.residual,
+                     "features_ms": ev[0].elapsed_time(ev[1]), "solve_ms": solve_ms,
+                     "ms_per_iteration": solve_ms / max(1, r.iters), "eig_calls": r.eig_calls,
+                     "jacobi_sweeps": r.eig_sweeps}
+        ctx.close()
+    return out
+
+
 def report(args, probs, world, ms_max, ms_local, stats, launches, iters, conv, clocks, peaks, other,
-           e2e, conv_all, tuned=None, finals=None):
+           e2e, conv_all, tuned=None, finals=None, large=None):
     from paper_2310_14087_gb300 import kot
     value = conv_all / (ms_max / 1e3)          # converged solves per second, all ranks
     stats, breakdown = stats
@@ -799,6 +846,10 @@ def report(args, probs, world, ms_max, ms_local, stats, launches, iters, conv, c
         "kernels_one_untimed_step": {k: {"launches": v.launches, "ms": round(v.ms, 3)}
                                      for k, v in breakdown.items() if v.launches},
     }
+    if large:
+        line["large_l"] = {"what": "fixed-iteration solves at C3's and C5's shapes (Sec. 5 regime; "
+                                   "1e-6 is not reached there in 200 iterations), one problem each, "
+                                   "after one warm-up solve", "precision": args.precision, **large}
     mv = breakdown.get("schur_matvec")
     if mv is not None and mv.launches:
         mpk = peaks.get("bf16_tflops_sustained", 1713.0) if args.precision == "mixed" else FP64_PEAK_TFLOPS
