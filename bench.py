@@ -277,7 +277,7 @@ def main():
     if args.autotune:
         # untimed: pick the emulated product's split counts and the Jacobi CTA count for this l
         tuned = dict(zip(("splits_3_slices", "splits_6_slices", "jacobi_ctas", "tile_n_3_slices",
-                          "tile_n_6_slices"),
+                          "tile_n_6_slices", "jacobi_threads"),
                          kot.Context(device=local_rank).autotune(p.l)))
     probs = [make_problem(args.workload, rank, k) for k in range(args.steps)]
     dprobs = [kot.DeviceProblem.from_problem(q, dev) for q in probs]
@@ -748,9 +748,11 @@ def errors_vs_oracle(F, ref, finals):
     return out
 
 
-# Large-l shapes in the Sec. 5 regime: Algorithm 2 does not reach 1e-6 there within 200 iterations,
-# so each is timed over a fixed number of iterations (one warm-up solve first).
-LARGE_L = [("paper_d10_n2000_l1024", 12), ("paper_d64_n4000_l2048", 5)]
+# Fixed-iteration lines (one warm-up solve first): the large-l shapes in the Sec. 5 regime, where
+# Algorithm 2 does not reach 1e-6 within 200 iterations, and BASELINE's literal C2 inputs
+# (Wishart Gaussians, sigma = the median distance, lambda2 = 1/n), where it stalls near 1e-2.
+LARGE_L = [("paper_d10_n2000_l1024", 12, None), ("paper_d64_n4000_l2048", 5, None),
+           ("literal_c2_wishart_d5_n1000_l300", 30, lambda: workloads.wishart_pair(seed=1))]
 
 
 def large_l_lines(prec, dev, local_rank):
@@ -760,9 +762,9 @@ def large_l_lines(prec, dev, local_rank):
     from paper_2310_14087_gb300 import kot
     out = {}
     stream = torch.cuda.Stream(device=dev)
-    for name, k in LARGE_L:
+    for name, k, gen in LARGE_L:
         ctx = kot.Context(device=local_rank, stream=stream.cuda_stream, precision=prec, max_iter=k)
-        p = make_problem(name, 0, 0)
+        p = gen() if gen else make_problem(name, 0, 0)
         dp = kot.DeviceProblem.from_problem(p, dev)
         g = torch.zeros(p.l, dtype=torch.float64, device=dev)
         build = lambda: ctx.build_features(dp.X, dp.Y, dp.Xf, dp.Yf, dp.sigma, dp.lambda1, dp.lambda2)
@@ -780,7 +782,7 @@ def large_l_lines(prec, dev, local_rank):
             ev[2].record(stream)
         ev[2].synchronize()
         solve_ms = ev[1].elapsed_time(ev[2])
-        out[name] = {**config_of(name), "iterations": r.iters, "residual_after": r.residual,
+        out[name] = {"d": p.d, "n": p.n, "l": p.l, "iterations": r.iters, "residual_after": r.residual,
                      "features_ms": ev[0].elapsed_time(ev[1]), "solve_ms": solve_ms,
                      "ms_per_iteration": solve_ms / max(1, r.iters), "eig_calls": r.eig_calls,
                      "jacobi_sweeps": r.eig_sweeps}
@@ -847,9 +849,11 @@ def report(args, probs, world, ms_max, ms_local, stats, launches, iters, conv, c
                                      for k, v in breakdown.items() if v.launches},
     }
     if large:
-        line["large_l"] = {"what": "fixed-iteration solves at C3's and C5's shapes (Sec. 5 regime; "
-                                   "1e-6 is not reached there in 200 iterations), one problem each, "
-                                   "after one warm-up solve", "precision": args.precision, **large}
+        line["large_l"] = {"what": "fixed-iteration solves, one problem each after one warm-up solve: "
+                                   "C3's and C5's shapes in the Sec. 5 regime (1e-6 is not reached "
+                                   "there in 200 iterations) and BASELINE's literal C2 inputs "
+                                   "(Algorithm 2 stalls near 1e-2 there)", "precision": args.precision,
+                           **large}
     mv = breakdown.get("schur_matvec")
     if mv is not None and mv.launches:
         mpk = peaks.get("bf16_tflops_sustained", 1713.0) if args.precision == "mixed" else FP64_PEAK_TFLOPS

@@ -269,12 +269,13 @@ kot_status kot_dense_product(kot_ctx* ctx, int M, int N, int K, double alpha, co
  * Times, on inputs it generates itself on the context's device and stream:
  *   - the emulated-FP64 product (three and six slices) at l x l x l for output-tile widths 64
  *     and 128 and split counts 1, 2, 3, 4, 6, 8, 12, 16;
- *   - a cold Jacobi decomposition of a symmetric l x l matrix for SMs/4, SMs/2 and SMs CTAs.
+ *   - a cold Jacobi decomposition of a symmetric l x l matrix for SMs/4, SMs/2 and SMs CTAs of
+ *     256, 512 and 1024 threads (the eigensolver's block size).
  * It records the fastest of each per size bucket (ceil log2 l) in a process-wide table for the
  * device.  Every later product of that size bucket and slice count, and every later decomposition
  * of that bucket (when kot_options.eig_ctas is 0), on any context of the device, uses the table.
- * choice (host, may be NULL, 5 ints) receives {splits with 3 slices, splits with 6 slices,
- * Jacobi CTAs, tile width with 3 slices, tile width with 6 slices}.
+ * choice (host, may be NULL, 6 ints) receives {splits with 3 slices, splits with 6 slices,
+ * Jacobi CTAs, tile width with 3 slices, tile width with 6 slices, Jacobi threads per CTA}.
  * Takes a few tens of milliseconds (longer for large l).  Returns KOT_ERR_INVALID for l outside
  * 1..32768. */
 kot_status kot_autotune(kot_ctx* ctx, int l, int* choice);

@@ -432,9 +432,11 @@ __global__ void __launch_bounds__(1024) k_dot_one(size_t n, const double* __rest
 //   pHp = p.Hp -> sc[3];  a = ee / pHp;  x += a p;  e -= a Hp;  ee' = |e|^2 -> sc[5+(cur^1)];
 //   p = e + (ee'/ee) p.
 // pHp <= 0: nothing is updated, sc[7] = 1 and sc[5+(cur^1)] = ee.
+// W (nw entries, may be null) += a Wp: a quantity carried along x, e.g. the rows of T[Phi*(x)].
 __global__ void __launch_bounds__(1024) k_cg_step(int n, const double* __restrict__ Hp, double* __restrict__ p,
                                                   double* __restrict__ x, double* __restrict__ e,
-                                                  double* __restrict__ sc, int cur) {
+                                                  double* __restrict__ sc, int cur, size_t nw,
+                                                  const double* __restrict__ Wp, double* __restrict__ W) {
   pdl_wait();
   pdl_trigger();
   __shared__ double sh[1024];
@@ -453,6 +455,8 @@ __global__ void __launch_bounds__(1024) k_cg_step(int n, const double* __restric
     return;
   }
   const double a = ee / pHp;
+  if (W)
+    for (size_t i = t; i < nw; i += 1024) W[i] = fma(a, Wp[i], W[i]);
   acc = 0.0;
   for (int i = t; i < n; i += 1024) {
     x[i] = fma(a, p[i], x[i]);
@@ -590,6 +594,73 @@ __global__ void k_xpby_ratio(size_t n, const double* __restrict__ x, const doubl
   const double b = *num / *den;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     y[i] = fma(b, y[i], x[i]);
+}
+
+// Z = sym(X - a S) - c I (the argument of the projection in Eq. 4.2 and in the EG steps; S null
+// reads as zero) and, if FX is given, FX = S + c I (the X part of the EG operator at the same
+// point, with a = 1); one thread per pair i <= j.
+__global__ void k_form_z(int l, const double* __restrict__ X, const double* __restrict__ S, double a, double c,
+                         double* __restrict__ Z, double* __restrict__ FX) {
+  pdl_wait();
+  pdl_trigger();
+  const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
+  if (i >= l || j >= l || j < i) return;
+  const size_t ij = (size_t)i * l + j, ji = (size_t)j * l + i;
+  if (i == j) {
+    const double sii = S ? S[ij] : 0.0;
+    Z[ij] = (X[ij] - a * sii) - c;
+    if (FX) FX[ij] = sii + c;
+    return;
+  }
+  const double sij = S ? S[ij] : 0.0, sji = S ? S[ji] : 0.0;
+  const double v = 0.5 * ((X[ij] - a * sij) + (X[ji] - a * sji));
+  Z[ij] = v;
+  Z[ji] = v;
+  if (FX) {
+    FX[ij] = sij;
+    FX[ji] = sji;
+  }
+}
+
+// out_i = s (Q gamma)_i - s z_i - v_i (one warp per row): the gradient of Eq. 4.1's Lagrangian in
+// gamma, i.e. r1 of Eq. 4.2, with v = Phi(X).
+__global__ void k_grad_gamma(int n, double s, const double* __restrict__ Q, const double* __restrict__ gamma,
+                             const double* __restrict__ z, const double* __restrict__ v,
+                             double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double* row = Q + (size_t)warp * n;
+  double acc = 0.0;
+  for (int j = lane; j < n; j += 32) acc = fma(row[j], gamma[j], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[warp] = (s * acc - s * z[warp]) - v[warp];
+}
+
+// D = X - P (elementwise over n2 entries) with partial sums of |x1|^2 (n1 entries) and |D|^2:
+// the residual block r2 of Eq. 4.2 and both norms of ||R(w)||; pairs as in k_two_norms.
+__global__ void k_sub_norms(size_t n1, const double* __restrict__ x1, size_t n2, const double* __restrict__ X,
+                            const double* __restrict__ P, double* __restrict__ D, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ double sh[256];
+  double s1 = 0.0, s2 = 0.0;
+  const size_t stride = (size_t)gridDim.x * 256;
+  for (size_t i = blockIdx.x * 256 + threadIdx.x; i < n1; i += stride) s1 = fma(x1[i], x1[i], s1);
+  for (size_t i = blockIdx.x * 256 + threadIdx.x; i < n2; i += stride) {
+    const double d = X[i] - P[i];
+    D[i] = d;
+    s2 = fma(d, d, s2);
+  }
+  s1 = block_sum<256>(s1, sh);
+  __syncthreads();
+  s2 = block_sum<256>(s2, sh);
+  if (threadIdx.x == 0) {
+    out[2 * blockIdx.x] = s1;
+    out[2 * blockIdx.x + 1] = s2;
+  }
 }
 
 __global__ void k_square(size_t n, const double* __restrict__ x, double* __restrict__ out) {
@@ -807,8 +878,9 @@ void sumsq_f64(cudaStream_t st, size_t n, const double* x, double* out, double* 
   KOT_LAUNCHED(2);
 }
 
-void cg_step(cudaStream_t st, int n, const double* Hp, double* p, double* x, double* e, double* sc, int cur) {
-  launch_pdl(k_cg_step, dim3(1), dim3(1024), 0, st, n, Hp, p, x, e, sc, cur);
+void cg_step(cudaStream_t st, int n, const double* Hp, double* p, double* x, double* e, double* sc, int cur,
+             size_t nw, const double* Wp, double* W) {
+  launch_pdl(k_cg_step, dim3(1), dim3(1024), 0, st, n, Hp, p, x, e, sc, cur, nw, Wp, W);
   KOT_CHECK_LAUNCH();
 }
 
@@ -838,6 +910,31 @@ void eig_norms(cudaStream_t st, size_t n1, const double* x, int rows, int cols, 
   const int nbk = kReduceBlocks / 2;   // partial holds kReduceBlocks doubles: nbk pairs
   launch_pdl(k_eig_norms, dim3(nbk), dim3(256), 0, st, n1, x, rows, cols, ld, nb, A, W, base, partial);
   launch_pdl(k_sum_pairs, dim3(1), dim3(256), 0, st, nbk, partial, out2);
+  KOT_LAUNCHED(2);
+}
+
+void form_z(cudaStream_t st, int l, const double* X, const double* S, double a, double c, double* Z, double* FX) {
+  launch_pdl(k_form_z, dim3(cdiv(l, 32), cdiv(l, 8)), dim3(32, 8), 0, st, l, X, S, a, c, Z, FX);
+  KOT_CHECK_LAUNCH();
+}
+
+void grad_gamma_fused(cudaStream_t st, int n, double s, const double* Q, const double* gamma, const double* z,
+                      const double* v, double* out) {
+  launch_pdl(k_grad_gamma, dim3(cdiv((size_t)n * 32, 256)), dim3(256), 0, st, n, s, Q, gamma, z, v, out);
+  KOT_CHECK_LAUNCH();
+}
+
+void sub_norms(cudaStream_t st, size_t n1, const double* x1, size_t n2, const double* X, const double* P,
+               double* D, double* out2, double* partial) {
+  const size_t n = std::max(n1, n2);
+  if (n <= kOneBlockN / 4) {
+    launch_pdl(k_sub_norms, dim3(1), dim3(256), 0, st, n1, x1, n2, X, P, D, out2);
+    KOT_CHECK_LAUNCH();
+    return;
+  }
+  const int nb = kReduceBlocks / 2;   // partial holds kReduceBlocks doubles: nb pairs
+  launch_pdl(k_sub_norms, dim3(nb), dim3(256), 0, st, n1, x1, n2, X, P, D, partial);
+  launch_pdl(k_sum_pairs, dim3(1), dim3(256), 0, st, nb, partial, out2);
   KOT_LAUNCHED(2);
 }
 

@@ -314,11 +314,13 @@ __device__ double block_reduce_sum(double v, double* sh) {
   return r;
 }
 
+// Threads per CTA of the cooperative kernel (its "block size"): 256, 512 (default) or 1024,
+// chosen per size bucket by the autotuner.
 constexpr int kCoopThreads = 512;
 
-template <typename T>
-__global__ void __launch_bounds__(kCoopThreads) k_jacobi_coop(CoopArgs<T> a) {
-  __shared__ double sh[kCoopThreads];
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_jacobi_coop(CoopArgs<T> a) {
+  __shared__ double sh[NT];
   const int lp = a.lp, l = a.l, half = lp / 2;
   const unsigned nb = gridDim.x;
   const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -591,6 +593,7 @@ int eig_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, dou
 
 namespace {
 int g_tuned_ctas[64][32] = {};
+int g_tuned_threads[64][32] = {};
 int l_bucket(int l) {
   int b = 0;
   while ((1 << b) < l && b < 31) ++b;
@@ -608,6 +611,25 @@ void set_tuned_jacobi_ctas(int dev, int l, int ctas) {
   g_tuned_ctas[dev][l_bucket(l)] = std::max(0, ctas);
 }
 
+int tuned_jacobi_threads(int dev, int l) {
+  if (dev < 0 || dev >= 64) return 0;
+  return g_tuned_threads[dev][l_bucket(l)];
+}
+
+void set_tuned_jacobi_threads(int dev, int l, int threads) {
+  if (dev < 0 || dev >= 64) return;
+  g_tuned_threads[dev][l_bucket(l)] = (threads == 256 || threads == 512 || threads == 1024) ? threads : 0;
+}
+
+namespace {
+// The cooperative kernel's instantiation for NT threads per CTA and its CTAs per SM.
+const void* coop_kernel(int nt) {
+  if (nt == 256) return (const void*)k_jacobi_coop<double, 256>;
+  if (nt == 1024) return (const void*)k_jacobi_coop<double, 1024>;
+  return (const void*)k_jacobi_coop<double, 512>;
+}
+}  // namespace
+
 int jacobi_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, double* P,
                    double* sig, JacobiWork& w, int max_sweeps, double* host_scal, int ctas) {
   const int lp = std::max(2, l + (l & 1));   // even, >= 2; a zero pad row/column never rotates
@@ -615,7 +637,10 @@ int jacobi_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
   int dev = 0, nsm = 0, per_sm = 0;
   KOT_CUDA(cudaGetDevice(&dev));
   KOT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  KOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_coop<double>, kCoopThreads, 0));
+  // threads per CTA: the caller's probe, else the autotuner's choice for this size bucket, else 512
+  int nt = w.threads_override > 0 ? w.threads_override : tuned_jacobi_threads(dev, l);
+  if (nt != 256 && nt != 1024) nt = kCoopThreads;
+  KOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_kernel(nt), nt, 0));
   if (per_sm < 1) throw Error{KOT_ERR_CUDA, "eig: cooperative kernel does not fit on an SM"};
   // one CTA per SM by default (fewer arrivals per barrier than several per SM), or the
   // autotuner's choice for this size bucket
@@ -665,8 +690,7 @@ int jacobi_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
     const double rflops = 24.0 * hb + 6.0 * (double)l * half;
     ProfScope ps(st, KC_JACOBI, rflops * (lp - 1), 8.0 * 2.0 * (2.0 * lp * (double)lp + (double)l * lp));
     void* args[] = {&a};
-    KOT_CUDA(cudaLaunchCooperativeKernel((const void*)k_jacobi_coop<double>, dim3(grid), dim3(kCoopThreads),
-                                         args, 0, st));
+    KOT_CUDA(cudaLaunchCooperativeKernel(coop_kernel(nt), dim3(grid), dim3(nt), args, 0, st));
     KOT_LAUNCHED(1);
   }
   int hflags[2] = {0, 0};

@@ -232,11 +232,8 @@ void phi_nd(kot_ctx* C, const double* X, double* out, double* tmp) {
 void grad_gamma(kot_ctx* C, const double* gamma, const double* X, double* out, double* vtmp,
                 double* mtmp) {
   const int l = C->l;
-  const double s = 1.0 / (2.0 * C->lambda2);
-  gemv_f64(C->st, l, s, C->Q.p, gamma, 0.0, out);
-  axpby(C->st, l, 1.0, out, -s, C->z.p, out);
   phi(C, X, vtmp, mtmp);
-  axpby(C->st, l, 1.0, out, -1.0, vtmp, out);
+  grad_gamma_fused(C->st, l, 1.0 / (2.0 * C->lambda2), C->Q.p, gamma, C->z.p, vtmp, out);
 }
 
 // Eigen-decompose Z (read only) into slot e (warm-started from `warm` if valid); reads the
@@ -287,13 +284,12 @@ void form_proj(kot_ctx* C, const double* Z, const EigSlot& e, double* out) {
   }
 }
 
-// M <- Pi_{S+}(M) with slot e (warm-started from itself)
-void proj_inplace(kot_ctx* C, double* M, EigSlot& e) {
+// out <- Pi_{S+}(sym(X - a S) - c I) with slot e (warm-started from itself); out may alias X.
+void proj_into(kot_ctx* C, const double* X, const double* S, double a, double c, double* out, EigSlot& e) {
   const int l = C->l;
-  copy_mat(C->st, l, l, M, l, C->M6.p, l);
-  symmetrize(C->st, l, C->M6.p);
+  form_z(C->st, l, X, S, a, c, C->M6.p, nullptr);
   eig_into(C, C->M6.p, e, &e);
-  form_proj(C, C->M6.p, e, M);
+  form_proj(C, C->M6.p, e, out);
 }
 
 // R(w) of Eq. (4.2) into r; eigen-decomposition of Z(w) into e.
@@ -305,23 +301,17 @@ void residual(kot_ctx* C, const double* gamma, const double* X, EigSlot& e, cons
   const int l = C->l;
   const size_t L2 = (size_t)l * l;
   phi_star(C, gamma, C->M1.p);
-  if (save_fv) {
-    copy_mat(C->st, l, l, C->M1.p, l, C->FvX.p, l);
-    add_diag(C->st, l, C->lambda1, C->FvX.p, l);               // F_X(v) = Phi*(gamma) + lambda1 I
-  }
-  axpby(C->st, L2, 1.0, X, -1.0, C->M1.p, C->M1.p);          // Z = X - Phi*(gamma)
-  add_diag(C->st, l, -C->lambda1, C->M1.p, l);                // ... - lambda1 I
-  symmetrize(C->st, l, C->M1.p);
-  eig_into(C, C->M1.p, e, warm);
-  form_proj(C, C->M1.p, e, C->M2.p);
-  axpby(C->st, L2, 1.0, X, -1.0, C->M2.p, r.r2.p);            // r2 = X - Pi(Z)
+  // Z = sym(X - Phi*(gamma)) - lambda1 I into M5; with save_fv, F_X(v) = Phi*(gamma) + lambda1 I
+  form_z(C->st, l, X, C->M1.p, 1.0, C->lambda1, C->M5.p, save_fv ? C->FvX.p : nullptr);
+  eig_into(C, C->M5.p, e, warm);
+  form_proj(C, C->M5.p, e, C->M2.p);
   grad_gamma(C, gamma, X, r.r1.p, C->v1.p, C->M3.p);           // r1
   if (save_fv) {
     KOT_CUDA(cudaMemcpyAsync(C->Fvg.p, r.r1.p, l * sizeof(double), cudaMemcpyDeviceToDevice, C->st));
     C->fv_valid = true;                                       // F_gamma(v) = r1(v)
   }
-  sumsq_f64(C->st, l, r.r1.p, C->scal.p, C->partial.p);
-  sumsq_f64(C->st, L2, r.r2.p, C->scal.p + 1, C->partial.p);
+  // r2 = X - Pi(Z) with |r1|^2 and |r2|^2 in one pass
+  sub_norms(C->st, l, r.r1.p, L2, X, C->M2.p, r.r2.p, C->scal.p, C->partial.p);
   fetch(C, 2);
   r.n1 = std::sqrt(C->hs[0]);
   r.n2 = std::sqrt(C->hs[1]);
@@ -630,10 +620,9 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
                        8.0 * (2.0 * L * L + 4.0 * a * L), 4.0 * a * L * L + 2.0 * L * L);
           schur_eig(C, e, mu, pv, C->M5.p, C->M6.p, Hp);
         }
-        // a = ||e||^2 / p^T H p: x += a p, e -= a H p, p = e + b p (one block, scalars on the
-        // device), then T[Phi*(x)] += a T[Phi*(p)]
-        cg_step(st, l, Hp, pv, dgam, ev, sc, cur);
-        axpy_ratio(st, (size_t)crow * l, sc + 5 + cur, sc + 3, 1.0, C->M5.p, Wx, nullptr);
+        // a = ||e||^2 / p^T H p: x += a p, e -= a H p, p = e + b p, and the carried rows of
+        // T[Phi*(x)] += a those of T[Phi*(p)] (one block, scalars on the device)
+        cg_step(st, l, Hp, pv, dgam, ev, sc, cur, (size_t)crow * l, C->M5.p, Wx);
         cur ^= 1;
         ++it;
       }
@@ -678,15 +667,12 @@ void eg_step(kot_ctx* C, double eta) {
     add_diag(st, l, C->lambda1, C->M1.p, l);                      // M1 = F_X(v)
   }
   axpby(st, l, 1.0, C->vg.p, -eta, C->v2.p, C->v4.p);             // gamma_h
-  axpby(st, L2, 1.0, C->vX.p, -eta, FX, C->M2.p);                 // X_v - eta F_X(v)
-  proj_inplace(C, C->M2.p, C->e1);                                // X_h
+  proj_into(C, C->vX.p, FX, eta, 0.0, C->M2.p, C->e1);            // X_h = Pi(X_v - eta F_X(v))
   // F at h
   grad_gamma(C, C->v4.p, C->M2.p, C->v3.p, C->v1.p, C->M3.p);
-  phi_star(C, C->v4.p, C->M1.p);
-  add_diag(st, l, C->lambda1, C->M1.p, l);
+  phi_star(C, C->v4.p, C->M1.p);                                  // F_X(h) = M1 + lambda1 I
   axpby(st, l, 1.0, C->vg.p, -eta, C->v3.p, C->vg.p);
-  axpby(st, L2, 1.0, C->vX.p, -eta, C->M1.p, C->vX.p);
-  proj_inplace(C, C->vX.p, C->e2);
+  proj_into(C, C->vX.p, C->M1.p, eta, eta * C->lambda1, C->vX.p, C->e2);
   C->fv_valid = false;                                            // v has moved
 }
 
@@ -1399,25 +1385,42 @@ kot_status kot_autotune(kot_ctx* C, int l, int* choice) {
     symmetrize(st, l, Cm.p);
     int nsm = 152;
     KOT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    int best_ctas = nsm;
+    int best_ctas = nsm, best_threads = 512;
     float best = 1e30f;
-    for (int ctas : {nsm / 4, nsm / 2, nsm}) {
-      if (ctas < 1) continue;
-      const float t = timed([&] {
-        eig_sym_f64(st, l, Cm.p, nullptr, P.p, sig.p, C->jw, kMaxSweeps, C->hs, ctas, 0);
-      }, 1);
-      if (t < best) {
-        best = t;
-        best_ctas = ctas;
+    std::vector<double> sig0, sig1((size_t)l);
+    for (int threads : {256, 512, 1024})
+      for (int ctas : {nsm / 4, nsm / 2, nsm}) {
+        if (ctas < 1) continue;
+        C->jw.threads_override = threads;
+        const float t = timed([&] {
+          eig_sym_f64(st, l, Cm.p, nullptr, P.p, sig.p, C->jw, kMaxSweeps, C->hs, ctas, 0);
+        }, 1);
+        // a launch shape is a candidate only if it gives the first shape's eigenvalues
+        KOT_CUDA(cudaMemcpyAsync(sig1.data(), sig.p, (size_t)l * sizeof(double), cudaMemcpyDeviceToHost, st));
+        KOT_CUDA(cudaStreamSynchronize(st));
+        if (sig0.empty()) sig0 = sig1;
+        double scale = 0.0, diff = 0.0;
+        for (int i = 0; i < l; ++i) {
+          scale = std::max(scale, std::fabs(sig0[i]));
+          diff = std::max(diff, std::fabs(sig1[i] - sig0[i]));
+        }
+        if (!(diff <= 1e-12 * std::max(scale, 1e-300))) continue;
+        if (t < best) {
+          best = t;
+          best_ctas = ctas;
+          best_threads = threads;
+        }
       }
-    }
+    C->jw.threads_override = 0;
     set_tuned_jacobi_ctas(dev, l, best_ctas);
+    set_tuned_jacobi_threads(dev, l, best_threads);
     if (choice) {
       choice[0] = best_split[0];
       choice[1] = best_split[1];
       choice[2] = best_ctas;
       choice[3] = best_bn[0];
       choice[4] = best_bn[1];
+      choice[5] = best_threads;
     }
     for (DevBuf<double>* b : {&A, &B, &Cm, &P, &sig}) b->release();
   });

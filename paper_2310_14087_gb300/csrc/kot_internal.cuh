@@ -185,8 +185,10 @@ void dot_f64(cudaStream_t st, int n, const double* x, const double* y, double* o
 void sumsq_f64(cudaStream_t st, size_t n, const double* x, double* out, double* partial);
 constexpr int kReduceBlocks = 128;   // size of the partial buffer the reductions need
 // One CG step with device-resident scalars (see k_cg_step in dense.cu): sc[5 + cur] = |e|^2 in,
-// sc[3] = p.Hp, sc[5 + (cur ^ 1)] = new |e|^2, sc[7] = 1 on non-positive curvature.
-void cg_step(cudaStream_t st, int n, const double* Hp, double* p, double* x, double* e, double* sc, int cur);
+// sc[3] = p.Hp, sc[5 + (cur ^ 1)] = new |e|^2, sc[7] = 1 on non-positive curvature; W (nw
+// entries, may be null) += (step length) Wp alongside x.
+void cg_step(cudaStream_t st, int n, const double* Hp, double* p, double* x, double* e, double* sc, int cur,
+             size_t nw = 0, const double* Wp = nullptr, double* W = nullptr);
 // out2[0] = |x|^2 (n1 entries), out2[1] = |a - b|^2 (n2 entries); partial: kReduceBlocks doubles
 void two_norms(cudaStream_t st, size_t n1, const double* x, size_t n2, const double* a, const double* b,
                double* out2, double* partial);
@@ -202,6 +204,14 @@ void eig_norms(cudaStream_t st, size_t n1, const double* x, int rows, int cols, 
 void eig_norms_comp(cudaStream_t st, int l, const double* x, int nb, const double* sig, double mu,
                     const double* A2, const double* U, const double* KK, const double* phi_at2,
                     const double* base, double* out2, double* partial);
+// Z = sym(X - a S) - c I (S null: zero); FX (may be null) = S + c I.  l x l, row-major.
+void form_z(cudaStream_t st, int l, const double* X, const double* S, double a, double c, double* Z, double* FX);
+// out = s Q gamma - s z - v (Q: n x n)
+void grad_gamma_fused(cudaStream_t st, int n, double s, const double* Q, const double* gamma, const double* z,
+                      const double* v, double* out);
+// D = X - P over n2 entries; out2[0] = |x1|^2 (n1 entries), out2[1] = |D|^2; partial: kReduceBlocks doubles
+void sub_norms(cudaStream_t st, size_t n1, const double* x1, size_t n2, const double* X, const double* P,
+               double* D, double* out2, double* partial);
 // out2 = the column sums of nb (s1, s2) pairs in partial
 void sum_pairs(cudaStream_t st, int nb, const double* partial, double* out2);
 // out[i] = x[i]^2 (out may alias x)
@@ -271,6 +281,7 @@ struct JacobiWork {
   // refinement of a warm basis (l x l each, ld l): ping-pong bases, Z X, X^T Z X, X^T X, I + E
   DevBuf<double> Xa, Xb, Y, S, G, F, lam;
   DevBuf<unsigned long long> mx;   // [max |E_ij| (i != j), max |I - X^T X|] as ordered bits
+  int threads_override = 0;        // > 0: threads per CTA of the Jacobi kernel (the autotuner's probes)
   int last_sweeps = 0;             // Jacobi sweeps of the last call
   int last_refine = 0;             // refinement steps of the last call (0: Jacobi was used)
   void release() {
@@ -358,6 +369,9 @@ void set_tuned_tile_width(int dev, int mn, int slices, int bn);
 // Autotuner table for the cooperative Jacobi eigensolver: CTAs per size bucket (0 = one per SM).
 int tuned_jacobi_ctas(int dev, int l);
 void set_tuned_jacobi_ctas(int dev, int l, int ctas);
+// ... and its threads per CTA (256, 512 or 1024; 0 = not tuned, 512)
+int tuned_jacobi_threads(int dev, int l);
+void set_tuned_jacobi_threads(int dev, int l, int threads);
 // gemm_f64's interface (C = alpha opA(A) diag(s) opB(B) + beta C, triangular/symmetric flags):
 // on the FP64 pipes when oz is null, else emulated on the tensor cores with oz->slices slices
 // (the triangular flags only cut work on the FP64 pipes; G_SYM is honoured by both).

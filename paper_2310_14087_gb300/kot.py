@@ -259,10 +259,10 @@ class Context:
         return self._check(lib().kot_profile(self.h, mask))
 
     def autotune(self, l: int):
-        """Tune the emulated product's tile widths and split counts and the Jacobi CTA count for
-        size l; returns (splits 3 slices, splits 6 slices, Jacobi CTAs, width 3 slices,
-        width 6 slices)."""
-        out = (C.c_int * 5)()
+        """Tune the emulated product's tile widths and split counts and the Jacobi CTA count and
+        threads per CTA for size l; returns (splits 3 slices, splits 6 slices, Jacobi CTAs,
+        width 3 slices, width 6 slices, Jacobi threads)."""
+        out = (C.c_int * 6)()
         self._check(lib().kot_autotune(self.h, l, out))
         return tuple(out)
 

@@ -64,3 +64,22 @@ def test_two_ranks_shard_problems_and_aggregate_the_job():
 def test_single_rank_totals_are_local():
     import bench
     assert bench.job_totals(5, 250.0, 1) == (5.0, 250.0, 20.0)
+
+
+def test_errors_vs_oracle_reports_distances():
+    # the bench line's distances of each form's result from the oracle's solve of the same
+    # problem: relative objective and gamma errors, and R(w) as the oracle evaluates it
+    import types
+    import bench
+    from oracle import kot_oracle as ko
+    from paper_2310_14087_gb300 import workloads as wl
+    p = wl.paper_regime(seed=2, d=2, n=100, l=50)
+    F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
+    ref = ko.ssn_solve(F, p.tol)
+    g = ref.gamma * (1 + 1e-7)
+    r = types.SimpleNamespace(objective=ko.objective(F, g), residual=ref.residual, iters=ref.iters)
+    out = bench.errors_vs_oracle(F, ref, {"fp64": (g, ref.X, r)})["fp64"]
+    assert out["rel_err_gamma"] == pytest.approx(1e-7, rel=1e-6)
+    assert out["rel_err_objective"] == pytest.approx(abs(r.objective - ref.objective) / abs(ref.objective))
+    assert out["residual_by_oracle"] == pytest.approx(ko.residual(F, g, ref.X).norm)
+    assert out["iters"] == out["oracle_iters"] == ref.iters

@@ -545,6 +545,45 @@ def test_mixed_residual_sample_at_l1024():
     assert N(norms)[2] == pytest.approx(ref.norm, rel=1e-9)
 
 
+_C5 = {}
+
+
+def _c5_features():
+    """BASELINE's C5 stand-in (d = 64, n = 4000, l = 2048, L2-normalised 10-cluster features,
+    sigma = the median distance): the oracle's features, built once for both forms."""
+    if not _C5:
+        p = wl.feature_like()
+        _C5["p"] = p
+        _C5["F"] = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
+    return _C5["p"], _C5["F"]
+
+
+@pytest.mark.parametrize("precision", [kot.FP64, kot.MIXED])
+def test_residual_sample_at_l2048(precision):
+    # the largest shape: features (with the jittered Cholesky of an ill-conditioned K) and the
+    # residual map at one point against the oracle's; the eigenvalues of Z come from a cold
+    # decomposition (no warm basis) at this size
+    p, F = _c5_features()
+    g, X = _point(F, 9, 0.3)
+    ref = ko.residual(F, g, X)
+    ctx = kot.Context(device=0, precision=precision)
+    ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
+    l = F.l
+    z, q2, eps = Z(l), Z(1), Z(1)
+    ctx.get_features(z=z, q2=q2, eps=eps)
+    np.testing.assert_allclose(N(z), F.z, rtol=1e-12, atol=1e-14 * np.abs(F.z).max())
+    assert N(q2)[0] == pytest.approx(F.q2, rel=1e-12)
+    assert N(eps)[0] == F.eps
+    r1, sig, norms = Z(l), Z(l), Z(3)
+    ctx.residual(T(g), T(X), r1, None, None, sig, norms)
+    zn = np.abs(ref.eig.sig).max()
+    # eigenvalues: 1e-16 l relative, the size-proportional backward error of an orthogonal
+    # similarity (2e-13 at l = 2048), with R from a different Cholesky of the jittered K
+    np.testing.assert_allclose(N(sig), ref.eig.sig, atol=1e-11 * zn)
+    np.testing.assert_allclose(N(r1), ref.r1, rtol=1e-8, atol=1e-8 * np.abs(ref.r1).max())
+    assert N(norms)[2] == pytest.approx(ref.norm, rel=1e-8)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_degenerate_sizes_both_forms(precision):
     # l = 1 (a scalar problem; closed form gamma = max(b/(2a), -lambda1/R11^2)) and the separable
