@@ -81,6 +81,7 @@ struct kot_ctx {
   DevBuf<double> M1, M2, M3, M4, M5, M6, TU, TV, TW, TG;
   DevBuf<double> Cb, A2, Wx;   // eigenbasis CG: P^T R, P^T at2 P, the carried rows for x (see schur_eig)
   DevBuf<double> KK, H0, phia2;   // Kt o Kt (Kt = R^T R); Q/(2 lambda2) + KK/mu; Phi(at2)
+  DevBuf<double> CbT;             // Cb^T, for the few-row form of the Schur operator
   DevBuf<double> v1, v2, v3, v4, v5, v6, w1, w2, w3;
   DevBuf<double> Fvg, FvX;     // F(v) of the EG iterate, from its last residual evaluation
   bool fv_valid = false;
@@ -146,7 +147,7 @@ void ensure(kot_ctx* C, int l) {
   for (DevBuf<double>* b : {&C->Q, &C->K, &C->R, &C->X, &C->vX, &C->tX, &C->dX, &C->M1, &C->M2,
                             &C->M3, &C->M4, &C->M5, &C->M6, &C->TU, &C->TV, &C->TW, &C->TG,
                             &C->Cb, &C->A2, &C->Wx, &C->rw.r2, &C->rv.r2, &C->rt.r2, &C->FvX,
-                            &C->Plast, &C->KK, &C->H0})
+                            &C->Plast, &C->KK, &C->H0, &C->CbT})
     b->alloc(L2);
   C->Fvg.alloc(L);
   for (DevBuf<double>* b : {&C->z, &C->w_mu, &C->w_nu, &C->c, &C->g, &C->vg, &C->tg, &C->dg,
@@ -391,10 +392,25 @@ void cg_gemm(kot_ctx* C, bool ta, bool tb, int M, int N, int K, const double* A,
 // Y: rows x l scratch.
 bool complement_form(const EigSlot& e, int l) { return l - e.nb > e.nb; }
 
+// Few carried rows (1 .. kSkinnyRows): the FP64 row and column kernels of newton.cu (CbT = Cb^T
+// formed once per direction), exact and two launches instead of two products and four launches.
+bool skinny_form(const EigSlot& e, int l) {
+  const int crow = complement_form(e, l) ? e.nb : l - e.nb;
+  return crow > 0 && crow <= kSkinnyRows;
+}
+
 void schur_eig(kot_ctx* C, const EigSlot& e, double mu, const double* p, double* W, double* Y, double* Hp) {
   const int l = C->l, nb = e.nb, na = l - nb;
   cudaStream_t st = C->st;
   const double* Cb = C->Cb.p;
+  if (skinny_form(e, l)) {
+    const bool comp = complement_form(e, l);
+    const int crow = comp ? nb : na, r0 = comp ? 0 : nb;
+    schur_rows(st, l, crow, r0, Cb, p, e.sig.p, mu, nb, comp ? 1 : 0, W, Y);
+    if (comp) schur_cols(st, l, crow, r0, C->CbT.p, Y, -2.0, C->H0.p, 1.0, p, mu, Hp);
+    else schur_cols(st, l, crow, r0, C->CbT.p, Y, 2.0, C->Q.p, 1.0 / (2.0 * C->lambda2), p, mu, Hp);
+    return;
+  }
   if (complement_form(e, l)) {
     if (nb == 0) {
       fill(st, l, 0.0, C->v5.p);
@@ -516,7 +532,10 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
   double* pv = C->v4.p;     // CG direction
   double* Hp = C->v6.p;
   const int cap = cg_tol_abs > 0 ? 10 * l + 50 : C->opt.cg_max_iter;
-  const bool refine = mixed(C);
+  // the few-row form of the operator runs in FP64 in both forms, so its directions need no
+  // FP64 re-check
+  const bool skinny = C->opt.schur_solver != 1 && skinny_form(e, l);
+  const bool refine = mixed(C) && !skinny;
   int total = 0, refined_steps = 0;
   bool met = false;
   // right-hand side: a1 = -r1 - Phi(r2 + T[r2])/(mu+1), at2 = -(r2 + T[r2])/(mu+1), formed
@@ -535,6 +554,7 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
   if (eigcg) {
     OzWork* oz = ozp(C);
     gemm_acc(st, oz, true, false, l, l, l, 1.0, e.P.p, l, C->R.p, l, nullptr, 0.0, C->Cb.p, l, G_KHI_COL);
+    if (skinny) transpose(st, l, C->Cb.p, C->CbT.p);
     gemm_acc(st, oz, true, false, l, l, l, 1.0, e.P.p, l, r.r2.p, l, nullptr, 0.0, C->TU.p, l, 0);
     gemm_acc(st, oz, false, false, l, l, l, 1.0, C->TU.p, l, e.P.p, l, nullptr, 0.0, C->TV.p, l, G_SYM);
     rhs_weights(st, l, nb, e.sig.p, mu, C->TV.p, C->A2.p);
@@ -836,7 +856,7 @@ kot_status kot_destroy(kot_ctx* C) {
   for (DevBuf<double>* b : {&C->Q, &C->K, &C->R, &C->z, &C->w_mu, &C->w_nu, &C->c, &C->g, &C->X,
                             &C->vg, &C->vX, &C->tg, &C->tX, &C->dg, &C->dX, &C->M1, &C->M2,
                             &C->M3, &C->M4, &C->M5, &C->M6, &C->TU, &C->TV, &C->TW, &C->TG,
-                            &C->Cb, &C->A2, &C->Wx, &C->KK, &C->H0, &C->phia2,
+                            &C->Cb, &C->A2, &C->Wx, &C->KK, &C->H0, &C->phia2, &C->CbT,
                             &C->v1, &C->v2, &C->v3, &C->v4, &C->v5, &C->v6, &C->w1, &C->w2,
                             &C->w3, &C->partial,
                             &C->scal, &C->bounds, &C->rw.r1, &C->rw.r2, &C->rv.r1, &C->rv.r2,

@@ -385,6 +385,14 @@ void gemm_acc(cudaStream_t st, OzWork* oz, bool ta, bool tb, int M, int N, int K
 // 1/mu - xi on alpha).  U null: in place on V.  See t_apply and schur_eig in kot_api.cu.
 void t_weights(cudaStream_t st, int l, int nb, const double* sig, double mu, int complement,
                double* V, const double* U = nullptr);
+// The Schur operator's rows and columns for few carried rows (crow <= 32; see newton.cu):
+// carry/W (crow x l) from rows r0.. of Cb and p; Hp = alpha H p + mu p + c diag(Cb_rows^T W Cb).
+constexpr int kSkinnyRows = 32;
+void schur_rows(cudaStream_t st, int l, int crow, int r0, const double* Cb, const double* p, const double* sig,
+                double mu, int nb, int complement, double* carry, double* W);
+void schur_cols(cudaStream_t st, int l, int crow, int r0, const double* CbT, const double* W, double c,
+                const double* H, double alpha, const double* p, double mu, double* Hp);
+void transpose(cudaStream_t st, int l, const double* A, double* B);   // B = A^T (l x l)
 // D = A2 - Psi o Vx (l x l): the eigenbasis form of dX = at2 - T[Phi*(x)] from the full Vx.
 void assemble_psi(cudaStream_t st, int l, int nb, const double* sig, double mu, const double* A2,
                   const double* Vx, double* D);

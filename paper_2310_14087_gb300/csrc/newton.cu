@@ -91,6 +91,111 @@ __global__ void k_eig_norms_comp(int l, const double* __restrict__ x, int nb, co
   }
 }
 
+// ---- the Schur operator of Algorithm 1 in the eigenbasis for few carried rows (<= 32): two FP64
+// kernels in place of two tensor-core products and four small launches.  With rows r0 .. r0 + crow
+// of Cb = P^T R (the alpha rows, G + G^T form, or the alpha-bar rows, complement form):
+//   k_schur_rows:  U[r][j] = sum_k Cb[r0 + r][k] p_k Cb[j][k],  W = weights o U   (one warp per j)
+//   k_schur_cols:  Y[r][i] = sum_j W[r][j] Cb[j][i],  v_i = c sum_r Cb[r0 + r][i] Y[r][i],
+//                  Hp_i = alpha (H p)_i + mu p_i + v_i                             (one warp per i)
+// (c = 2, H = Q, alpha = 1/(2 lambda2) for G + G^T; c = -2, H = H0 = Q/(2 lambda2) + (Kt o Kt)/mu,
+// alpha = 1 for the complement form).  A contraction this small is bound by latency, not by the
+// multiply rate: 2 crow l^2 FP64 FMAs spread over every SM take a few microseconds, and FP64 makes
+// the CG iterates exact instead of three-slice accurate.
+__global__ void __launch_bounds__(256) k_schur_rows(int l, int crow, int r0, const double* __restrict__ Cb,
+                                                    const double* __restrict__ p, const double* __restrict__ sig,
+                                                    double mu, int nb, int complement, double* __restrict__ carry,
+                                                    double* __restrict__ W) {
+  pdl_wait();
+  pdl_trigger();
+  const int j = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;   // 8 warps per column j
+  if (j >= l) return;
+  const double* b = Cb + (size_t)j * l;
+  for (int r = warp; r < crow; r += 8) {
+    const double* a = Cb + (size_t)(r0 + r) * l;
+    double acc0 = 0.0, acc1 = 0.0;
+    int k = lane;
+    for (; k + 32 < l; k += 64) {   // two independent chains keep loads in flight
+      acc0 = fma(a[k] * p[k], b[k], acc0);
+      acc1 = fma(a[k + 32] * p[k + 32], b[k + 32], acc1);
+    }
+    if (k < l) acc0 = fma(a[k] * p[k], b[k], acc0);
+    double acc = acc0 + acc1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      const double w = acc * t_weight(r, j, nb, sig, mu, complement);
+      W[(size_t)r * l + j] = w;
+      carry[(size_t)r * l + j] = complement ? acc : w;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_schur_cols(int l, int crow, int r0, const double* __restrict__ CbT,
+                                                    const double* __restrict__ W, double c,
+                                                    const double* __restrict__ H, double alpha,
+                                                    const double* __restrict__ p, double mu,
+                                                    double* __restrict__ Hp) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ double part[8][2];
+  const int i = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;   // 8 warps per column i
+  if (i >= l) return;
+  const double* col = CbT + (size_t)i * l;   // column i of Cb
+  // rows of W Cb at column i, each weighted by Cb[r0 + r][i]; warp w takes rows w, w + 8, ...
+  double v = 0.0;
+  for (int r = warp; r < crow; r += 8) {
+    const double* w = W + (size_t)r * l;
+    double acc0 = 0.0, acc1 = 0.0;
+    int j = lane;
+    for (; j + 32 < l; j += 64) {
+      acc0 = fma(w[j], col[j], acc0);
+      acc1 = fma(w[j + 32], col[j + 32], acc1);
+    }
+    if (j < l) acc0 = fma(w[j], col[j], acc0);
+    double acc = acc0 + acc1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    v = fma(col[r0 + r], acc, v);
+  }
+  // (H p)_i, the k range split over the 8 warps
+  const double* h = H + (size_t)i * l;
+  double hp = 0.0;
+  for (int k = threadIdx.x; k < l; k += 256) hp = fma(h[k], p[k], hp);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) hp += __shfl_xor_sync(0xffffffffu, hp, o);
+  if (lane == 0) {
+    part[warp][0] = v;
+    part[warp][1] = hp;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sv = 0.0, sh = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      sv += part[q][0];
+      sh += part[q][1];
+    }
+    Hp[i] = fma(mu, p[i], alpha * sh) + c * sv;
+  }
+}
+
+// B = A^T (l x l)
+__global__ void k_transpose(int l, const double* __restrict__ A, double* __restrict__ B) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ double t[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int i = by + y, j = bx + threadIdx.x;
+    if (i < l && j < l) t[y][threadIdx.x] = A[(size_t)i * l + j];
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int i = bx + y, j = by + threadIdx.x;
+    if (i < l && j < l) B[(size_t)i * l + j] = t[threadIdx.x][y];
+  }
+}
+
 // D = A2 - Psi o Vx over l x l (Psi of Sec. 4.3: 1/mu on alpha x alpha, xi on alpha x alpha-bar and
 // its transpose, 0 on alpha-bar x alpha-bar): the eigenbasis form of dX = at2 - T[Phi*(x)].
 __global__ void k_assemble_psi(int l, int nb, const double* __restrict__ sig, double mu,
@@ -183,6 +288,23 @@ void eig_norms_comp(cudaStream_t st, int l, const double* x, int nb, const doubl
              partial);
   sum_pairs(st, nbk, partial, out2);
   KOT_LAUNCHED(1);
+}
+
+void schur_rows(cudaStream_t st, int l, int crow, int r0, const double* Cb, const double* p, const double* sig,
+                double mu, int nb, int complement, double* carry, double* W) {
+  launch_pdl(k_schur_rows, dim3(l), dim3(256), 0, st, l, crow, r0, Cb, p, sig, mu, nb, complement, carry, W);
+  KOT_CHECK_LAUNCH();
+}
+
+void schur_cols(cudaStream_t st, int l, int crow, int r0, const double* CbT, const double* W, double c,
+                const double* H, double alpha, const double* p, double mu, double* Hp) {
+  launch_pdl(k_schur_cols, dim3(l), dim3(256), 0, st, l, crow, r0, CbT, W, c, H, alpha, p, mu, Hp);
+  KOT_CHECK_LAUNCH();
+}
+
+void transpose(cudaStream_t st, int l, const double* A, double* B) {
+  launch_pdl(k_transpose, dim3(cdiv(l, 32), cdiv(l, 32)), dim3(32, 8), 0, st, l, A, B);
+  KOT_CHECK_LAUNCH();
 }
 
 void assemble_psi(cudaStream_t st, int l, int nb, const double* sig, double mu, const double* A2,
