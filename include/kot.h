@@ -92,6 +92,13 @@ typedef struct {
   int gram_fp32;           /* kot_build_features: 1 = the Gram matrices Q and K (Sec. 3) from FP32
                               distances and exponentials (entries ~1e-7 relative to FP64; the
                               embeddings, q2, z and the Cholesky stay FP64); 0 = FP64 (default) */
+  double tc_min_flops;     /* mixed form: a product of fewer multiply-add flops (2 M N K, halved
+                              for a symmetric result) runs exact on the FP64 pipes instead of
+                              the tensor cores, where the emulated product's three launches take
+                              longer (default 8e6: l x l x l products up to l ~ 158, and the
+                              projection's l x l x min(|alpha|, |alpha-bar|) ones); CG directions
+                              whose products all fall below it need no FP64 re-check;
+                              0 = every product on the tensor cores                        */
 } kot_options;
 
 typedef struct {

@@ -767,6 +767,70 @@ double gemm_macs(int M, int N, int K, int flags) {
   return macs;
 }
 
+// Short inner dimension (K <= kLowK, e.g. the l x l x min(|alpha|, |alpha-bar|) product of the
+// projection, Eq. (4.4)): C = alpha A diag(s) B^T + beta C with A (M x K) and B (N x K) row-major.
+// One 32 x 32 tile of C per block with both K-wide panels staged whole in shared memory, so the
+// kernel is one pass over C; the stream-K GEMM spends most of its time on set-up at such K.
+// G_SYM: blocks enumerate the tiles on or above the diagonal and store like sk_store.
+constexpr int kLowK = 64;
+__global__ void __launch_bounds__(256) k_gemm_f64_lowk(int M, int N, int K, double alpha,
+                                                       const double* __restrict__ A, int lda,
+                                                       const double* __restrict__ B, int ldb,
+                                                       const double* __restrict__ s, double beta,
+                                                       double* C, int ldc, int sym, int tn) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ double sA[32][kLowK + 1], sB[32][kLowK + 1];
+  int bi, bj;
+  if (sym) {
+    int t = blockIdx.x, len = tn;
+    bi = 0;
+    while (t >= len) {
+      t -= len;
+      ++bi;
+      --len;
+    }
+    bj = bi + t;
+  } else {
+    bi = blockIdx.y;
+    bj = blockIdx.x;
+  }
+  const int m0 = bi * 32, n0 = bj * 32;
+  for (int idx = threadIdx.x; idx < 32 * K; idx += blockDim.x) {
+    const int r = idx / K, k = idx - r * K;
+    double va = 0.0, vb = 0.0;
+    if (m0 + r < M) {
+      va = A[(size_t)(m0 + r) * lda + k];
+      if (s) va *= s[k];
+    }
+    if (n0 + r < N) vb = B[(size_t)(n0 + r) * ldb + k];
+    sA[r][k] = va;
+    sB[r][k] = vb;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // column n0 + tx, rows m0 + ty + 8 q
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = 0; k < K; ++k) {
+    const double vb = sB[tx][k];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = fma(sA[ty + 8 * q][k], vb, acc[q]);
+  }
+  const int gn = n0 + tx;
+  if (gn >= N) return;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int gm = m0 + ty + 8 * q;
+    if (gm >= M || (sym && gn < gm)) continue;
+    const double v = alpha * acc[q];
+    double* cp = &C[(size_t)gm * ldc + gn];
+    *cp = (beta == 0.0) ? v : v + beta * (*cp);
+    if (sym && gn > gm) {
+      double* cm = &C[(size_t)gn * ldc + gm];
+      *cm = (beta == 0.0) ? v : v + beta * (*cm);
+    }
+  }
+}
+
 }  // namespace
 
 void gemm_f64(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alpha,
@@ -779,6 +843,15 @@ void gemm_f64(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alp
   if (K <= 0) {   // C = beta C
     if (beta == 0.0)
       for (int i = 0; i < M; ++i) KOT_CUDA(cudaMemsetAsync(C + (size_t)i * ldc, 0, N * sizeof(double), st));
+    return;
+  }
+  if (K <= kLowK && !ta && tb && (flags & ~G_SYM) == 0) {
+    const int tm = cdiv(M, 32), tn = cdiv(N, 32);
+    const bool sym = (flags & G_SYM) != 0;
+    const dim3 grid = sym ? dim3(tn * (tn + 1) / 2) : dim3(tn, tm);
+    launch_pdl(k_gemm_f64_lowk, grid, dim3(256), 0, st, M, N, K, alpha, A, lda, B, ldb, s, beta, C, ldc,
+               sym ? 1 : 0, tn);
+    KOT_CHECK_LAUNCH();
     return;
   }
   int dev = 0, nsm = 0;

@@ -28,7 +28,7 @@ struct Range {
 }  // namespace
 
 // layouts the ctypes binding mirrors (LP64, natural alignment)
-static_assert(sizeof(kot_options) == 176, "kot_options layout");
+static_assert(sizeof(kot_options) == 184, "kot_options layout");
 static_assert(sizeof(kot_result) == 96, "kot_result layout");
 
 namespace {
@@ -135,6 +135,7 @@ void set_defaults(kot_options* o) {
   o->batch_workers = 0;
   o->eig_refine = 5;
   o->schur_solver = 0;
+  o->tc_min_flops = 8e6;
 }
 
 bool pos_finite(double v) { return std::isfinite(v) && v > 0.0; }
@@ -370,10 +371,15 @@ void t_apply(kot_ctx* C, const EigSlot& e, double mu, const double* S, double* o
 // application, against 2 l^3 + 4 min(|alpha|, |alpha-bar|) l^2 multiply-adds for
 // phi_star / T / phi.  Products run at the phase's precision (three slices inside tensor-core CG).
 // Out: W (|alpha| x l, ld l), Hp = Q p/(2 lambda2) + mu p + Phi(T[Phi*(p)]); Y: |alpha| x l scratch.
+// Products small enough for gemm_acc's FP64 route (OzWork::f64_below) run exact in either phase.
+bool cg_products_exact(const kot_ctx* C, int rows) {
+  return 2.0 * rows * (double)C->l * C->l < C->oz.f64_below;
+}
+
 void cg_gemm(kot_ctx* C, bool ta, bool tb, int M, int N, int K, const double* A, const double* B,
              const double* s, double* out) {
   const int l = C->l;
-  if (mixed(C))
+  if (mixed(C) && 2.0 * M * (double)N * K >= C->oz.f64_below)
     gemm_oz(C->st, C->oz, M, N, K, TcOperand{A, l, ta, s}, TcOperand{B, l, !tb, nullptr}, kCgSlices, 1.0, 0.0,
             out, l, false);
   else
@@ -532,10 +538,12 @@ int newton_direction(kot_ctx* C, const ResState& r, const EigSlot& e, double mu,
   double* pv = C->v4.p;     // CG direction
   double* Hp = C->v6.p;
   const int cap = cg_tol_abs > 0 ? 10 * l + 50 : C->opt.cg_max_iter;
-  // the few-row form of the operator runs in FP64 in both forms, so its directions need no
-  // FP64 re-check
+  // the few-row form of the operator, and products small enough for the FP64 GEMM, run in FP64
+  // in both forms, so their directions need no FP64 re-check
   const bool skinny = C->opt.schur_solver != 1 && skinny_form(e, l);
-  const bool refine = mixed(C) && !skinny;
+  const int nb0 = e.nb, crow0 = complement_form(e, l) ? nb0 : l - nb0;
+  const bool exact_ops = skinny || (C->opt.schur_solver != 1 && cg_products_exact(C, crow0));
+  const bool refine = mixed(C) && !exact_ops;
   int total = 0, refined_steps = 0;
   bool met = false;
   // right-hand side: a1 = -r1 - Phi(r2 + T[r2])/(mu+1), at2 = -(r2 + T[r2])/(mu+1), formed
@@ -786,6 +794,7 @@ kot_status run(kot_ctx* C, const std::function<void()>& body) {
     C->force64 = false;
     C->in_solve = false;
     C->jw.oz = C->opt.precision == KOT_MIXED ? &C->oz : nullptr;
+    C->oz.f64_below = C->opt.tc_min_flops;
   }
   try {
     body();
@@ -821,6 +830,7 @@ kot_status kot_create(kot_ctx** out, const kot_options* opt) {
       !(o.beta2 > 0) || !(o.theta0 > 0) || !(o.theta_min > 0) || !(o.theta_max >= o.theta_min) ||
       !(o.jitter >= 0) || !(o.jitter_max >= o.jitter) || o.eig_ctas < 0 || !(o.mixed_switch >= 0) || o.batch_workers < 0 || o.eig_refine < 0 ||
       (o.schur_solver != 0 && o.schur_solver != 1) || (o.gram_fp32 != 0 && o.gram_fp32 != 1) ||
+      !(o.tc_min_flops >= 0 && std::isfinite(o.tc_min_flops)) ||
       (o.precision != KOT_FP64 && o.precision != KOT_MIXED))
     return KOT_ERR_INVALID;
   int ndev = 0;

@@ -343,6 +343,10 @@ struct OzWork {
   int slices = 6;
   int splits_override = 0;       // > 0: use this split count (the autotuner's probes)
   int bn_override = 0;           // 64 or 128: use this output-tile width (the autotuner's probes)
+  // gemm_acc sends products of fewer multiply-add flops (2 M N K, halved for a symmetric result)
+  // to the FP64 GEMM: below about this size the three launches of the emulated product cost
+  // more than the FP64 pipes need for the whole product (kot_options.tc_min_flops)
+  double f64_below = 8e6;
   // last TMA descriptors (CUtensorMap, 128 bytes) and the (buffer, rows, cols) they describe
   alignas(64) unsigned char map_a[128], map_b[128];
   const void* key_a = nullptr;

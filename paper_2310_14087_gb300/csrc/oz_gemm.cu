@@ -781,7 +781,9 @@ int gemm_oz_error(cudaStream_t st, OzWork& w) {
 void gemm_acc(cudaStream_t st, OzWork* oz, bool ta, bool tb, int M, int N, int K, double alpha,
               const double* A, int lda, const double* B, int ldb, const double* s, double beta,
               double* C, int ldc, int flags) {
-  if (!oz) return gemm_f64(st, ta, tb, M, N, K, alpha, A, lda, B, ldb, s, beta, C, ldc, flags);
+  const double work = 2.0 * M * N * K * ((flags & G_SYM) ? 0.5 : 1.0);
+  if (!oz || work < oz->f64_below)
+    return gemm_f64(st, ta, tb, M, N, K, alpha, A, lda, B, ldb, s, beta, C, ldc, flags);
   // gemm_f64's op(B) is K x N; the tensor-core form takes it as N rows of K
   gemm_oz(st, *oz, M, N, K, TcOperand{A, lda, ta, s}, TcOperand{B, ldb, !tb, nullptr}, oz->slices, alpha,
           beta, C, ldc, (flags & G_SYM) != 0);

@@ -35,7 +35,7 @@ class Options(C.Structure):
                 ("jitter_max", C.c_double), ("use_eg", C.c_int), ("record_history", C.c_int),
                 ("eig_ctas", C.c_int), ("mixed_switch", C.c_double),
                 ("batch_workers", C.c_int), ("eig_refine", C.c_int), ("schur_solver", C.c_int),
-                ("gram_fp32", C.c_int)]
+                ("gram_fp32", C.c_int), ("tc_min_flops", C.c_double)]
 
 
 class Result(C.Structure):

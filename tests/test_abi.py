@@ -46,9 +46,9 @@ def test_default_options_follow_the_paper(lib):
 
 
 def test_struct_layouts_match_header(lib):
-    # kot_options: int, pointer, 4 ints, 13 doubles, 3 ints, 1 double, 3 ints (natural alignment;
+    # kot_options: int, pointer, 4 ints, 13 doubles, 3 ints, 1 double, 4 ints, 1 double (natural alignment;
     # the library asserts the same sizes at compile time)
-    assert ctypes.sizeof(kot.Options) == 8 * 4 + 13 * 8 + 16 + 8 + 16
+    assert ctypes.sizeof(kot.Options) == 8 * 4 + 13 * 8 + 16 + 8 + 16 + 8
     assert ctypes.sizeof(kot.Result) == 5 * 4 + 4 + 7 * 8 + 16
 
 

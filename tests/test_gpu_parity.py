@@ -147,7 +147,7 @@ def test_sqmr_newton_direction_matches_oracle(name, scale, mu):
 def test_solve_with_sqmr(precision):
     p = WORKLOADS["paper_d2_l50"]()
     F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
-    ctx = kot.Context(device=0, precision=precision, schur_solver=1)
+    ctx = kot.Context(device=0, precision=precision, schur_solver=1, tc_min_flops=0)
     ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
     g, X = Z(p.l), Z(p.l, p.l)
     res = ctx.ssn_solve(p.tol, g, X)
@@ -302,7 +302,8 @@ def test_pure_eg_matches_oracle(precision, eta):
     for _ in range(steps):
         g_ref, X_ref = ko.eg_step(F, g_ref, X_ref, ref_eta)
         ref_hist.append(ko.residual(F, g_ref, X_ref).norm)
-    ctx = kot.Context(device=0, precision=precision, max_iter=steps, eg_step=eta, record_history=1)
+    ctx = kot.Context(device=0, precision=precision, max_iter=steps, eg_step=eta, record_history=1,
+                      tc_min_flops=0)
     ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
     g, X = Z(p.l), Z(p.l, p.l)
     res = ctx.eg_solve(1e-12, g, X, allow_no_convergence=True)
@@ -369,7 +370,7 @@ def test_tiny_and_odd_sizes(l, precision):
     # the oracle reproduces at the returned iterate
     p = wl.paper_regime(seed=40 + l, d=2, n=30, l=l)
     F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
-    ctx = kot.Context(device=0, precision=precision, max_iter=30)
+    ctx = kot.Context(device=0, precision=precision, max_iter=30, tc_min_flops=0)
     ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
     z = Z(l)
     ctx.get_features(None, None, None, z, None, None, None, None, None)
@@ -404,13 +405,13 @@ def test_resume_from_a_checkpoint(precision):
     # the resumed solve reaches the tolerance at the same optimum as an uninterrupted one
     p = WORKLOADS["paper_d2_l50"]()
     F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
-    ctx = kot.Context(device=0, precision=precision, max_iter=3)
+    ctx = kot.Context(device=0, precision=precision, max_iter=3, tc_min_flops=0)
     ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
     g, X = Z(p.l), Z(p.l, p.l)
     r1 = ctx.ssn_solve(p.tol, g, X, allow_no_convergence=True)
     assert r1.status == kot.ERR_NO_CONVERGENCE and r1.iters == 3
     ckpt_g, ckpt_X = g.clone(), X.clone()
-    c2 = kot.Context(device=0, precision=precision)
+    c2 = kot.Context(device=0, precision=precision, tc_min_flops=0)
     c2.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
     g2, X2 = Z(p.l), Z(p.l, p.l)
     r2 = c2.ssn_solve(p.tol, g2, X2, ckpt_g, ckpt_X)
@@ -457,7 +458,7 @@ def test_error_paths():
 def test_mixed_newton_direction_close_to_oracle(name, scale, mu):
     p = WORKLOADS[name]()
     F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
-    ctx = kot.Context(device=0, precision=kot.MIXED)
+    ctx = kot.Context(device=0, precision=kot.MIXED, tc_min_flops=0)
     ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
     g, X = _point(F, 11, scale)
     res = ko.residual(F, g, X)
@@ -490,7 +491,7 @@ def test_mixed_residual_matches_oracle(name, scale):
     # oracle's FP64 one to a small multiple of the FP64 tolerances
     p = WORKLOADS[name]()
     F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
-    ctx = kot.Context(device=0, precision=kot.MIXED)
+    ctx = kot.Context(device=0, precision=kot.MIXED, tc_min_flops=0)
     ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
     g, X = _point(F, 7, scale)
     ref = ko.residual(F, g, X)
@@ -588,7 +589,7 @@ def test_residual_sample_at_l2048(precision):
 def test_degenerate_sizes_both_forms(precision):
     # l = 1 (a scalar problem; closed form gamma = max(b/(2a), -lambda1/R11^2)) and the separable
     # case Q = qI, R = I (gamma_i = max(z_i/q, -lambda1)) in both forms
-    ctx = kot.Context(device=0, precision=precision, max_iter=400)
+    ctx = kot.Context(device=0, precision=precision, max_iter=400, tc_min_flops=0)
     Q, R, lam1, lam2, z1 = np.array([[1.7]]), np.array([[0.8]]), 0.05, 0.1, -0.5
     ctx.set_features(T(Q), T(np.array([z1])), 1.0, T(R), lam1, lam2)
     g = Z(1)
@@ -606,18 +607,26 @@ def test_degenerate_sizes_both_forms(precision):
 
 
 @pytest.mark.parametrize("name", ["paper_d2_l50", "paper_d5_l97"])
-def test_mixed_solve_gates(name):
+@pytest.mark.parametrize("tc_min_flops", [0.0, None])
+def test_mixed_solve_gates(name, tc_min_flops):
     p = WORKLOADS[name]()
     F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
-    ctx = kot.Context(device=0, precision=kot.MIXED)
+    kw = {} if tc_min_flops is None else {"tc_min_flops": tc_min_flops}
+    ctx = kot.Context(device=0, precision=kot.MIXED, **kw)
     ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
     g, X = Z(p.l), Z(p.l, p.l)
     ctx.profile((1 << kot.KERNEL_CLASSES.index("gemm_oz")) | (1 << kot.KERNEL_CLASSES.index("gemm_f64")))
     res = ctx.ssn_solve(p.tol, g, X)
     assert res.status == kot.OK
-    # every O(l^3) product ran on the tensor cores (CG: 3 slices; FP64 accuracy: 6 slices)
-    assert ctx.profile_read(kot.KERNEL_CLASSES.index("gemm_oz")).launches > 0
-    assert ctx.profile_read(kot.KERNEL_CLASSES.index("gemm_f64")).launches == 0
+    oz = ctx.profile_read(kot.KERNEL_CLASSES.index("gemm_oz")).launches
+    f64 = ctx.profile_read(kot.KERNEL_CLASSES.index("gemm_f64")).launches
+    if tc_min_flops == 0.0:
+        # every O(l^3) product ran on the tensor cores (CG: 3 slices; FP64 accuracy: 6 slices)
+        assert oz > 0 and f64 == 0
+    else:
+        # the default routes products below 8e6 multiply-add flops (here every l x l x l one,
+        # 2 l^3 <= 1.9e6) to the FP64 GEMM
+        assert oz == 0 and f64 > 0
     check = ko.residual(F, N(g), N(X))
     assert check.norm <= p.tol * (1 + 1e-6)          # the oracle confirms the stopping test
     fstar, gstar = _optimum(F)

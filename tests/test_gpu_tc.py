@@ -66,7 +66,11 @@ def test_three_pieces_match_fp64(M, N, K, ta, tb):
 
 
 FP64_SHAPES = SHAPES + [(300, 300, 300, 1, 0), (22, 300, 300, 1, 0), (300, 300, 22, 0, 0),
-                        (16, 16, 1, 0, 1), (513, 511, 1025, 0, 0)]
+                        (16, 16, 1, 0, 1), (513, 511, 1025, 0, 0),
+                        # K <= 64 with op(B) given as N x K rows: the one-pass short-K kernel
+                        # (ragged 32 x 32 tiles, K = 1 and K = 64), and K = 65 just past it
+                        (300, 300, 18, 0, 0), (33, 65, 64, 0, 0), (257, 31, 63, 0, 0),
+                        (1, 700, 40, 0, 0), (700, 1, 1, 0, 0), (97, 97, 65, 0, 0)]
 
 
 @pytest.mark.parametrize("M,N,K,ta,tb", FP64_SHAPES)
