@@ -493,11 +493,16 @@ int jacobi_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
 
 namespace {
 
-// Refinement thresholds on max |E_ij|: above kRefineGiveUp the warm basis is too far for the
-// quadratic regime (or a pair is degenerate) and Jacobi takes over; at or below w.refine_done
-// (1e-8 unless the caller asks otherwise) the step just taken leaves an error of order
-// refine_done^2, so it is the last.
-constexpr double kRefineGiveUp = 0.05;
+// Refinement thresholds on max |E_ij| (and on the loss of orthogonality max |I - X^T X|): a
+// first correction above kRefineStart means the warm basis is too far for the iteration (or a
+// pair is degenerate), and a later one that is not below kRefineContract times its predecessor
+// means it is not converging; either way Jacobi takes over.  Converging steps contract the error
+// about quadratically (0.4 -> 0.16 -> 0.03 -> 1e-3), so a start of a few tenths still finishes in
+// the step budget at a fraction of the cost of Jacobi sweeps.  At or below w.refine_done (1e-8
+// unless the caller asks otherwise) the step just taken leaves an error of order refine_done^2,
+// so it is the last.
+constexpr double kRefineStart = 0.5;
+constexpr double kRefineContract = 0.5;
 
 // Refine the warm basis into P, sig (ascending).  Returns the steps taken, or 0 if the iteration
 // gave up (P and sig are then untouched).
@@ -523,6 +528,7 @@ int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
     X = w.Xa.p + l;
     ldX = ldx;
   }
+  double prev_me = 0.0;
   for (int k = 0; k < max_steps; ++k) {
     const double* S;
     const double* G;
@@ -559,7 +565,9 @@ int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
     double me, mr;
     std::memcpy(&me, &hm[0], sizeof(double));
     std::memcpy(&mr, &hm[1], sizeof(double));
-    if (!(me <= kRefineGiveUp) || !(mr <= kRefineGiveUp)) return 0;
+    const double cap = k == 0 ? kRefineStart : kRefineContract * prev_me;
+    if (!(me <= cap) || !(mr <= kRefineStart)) return 0;
+    prev_me = me;
     X = Xn;
     ldX = ldx;
     if (me <= w.refine_done && mr <= w.refine_done) {
@@ -577,14 +585,17 @@ int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
 
 int eig_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, double* P,
                 double* sig, JacobiWork& w, int max_sweeps, double* host_scal, int ctas,
-                int max_refine) {
+                int max_refine, const double* warm2) {
   w.last_sweeps = 0;
   w.last_refine = 0;
-  if (warm && max_refine > 0) {
-    const int k = refine_sym_f64(st, l, Z, warm, P, sig, w, max_refine);
-    if (k > 0) {
-      w.last_refine = k;
-      return 0;
+  if (max_refine > 0) {
+    for (const double* start : {warm, warm2}) {
+      if (!start) continue;
+      const int k = refine_sym_f64(st, l, Z, start, P, sig, w, max_refine);
+      if (k > 0) {
+        w.last_refine = k;
+        return 0;
+      }
     }
   }
   w.last_sweeps = jacobi_sym_f64(st, l, Z, warm, P, sig, w, max_sweeps, host_scal, ctas);

@@ -249,12 +249,17 @@ void eig_into(kot_ctx* C, const double* Z, EigSlot& e, const EigSlot* warm) {
   // back to Jacobi sweeps when it is too far off.
   const double* wp = (warm && warm->valid && !warm->trivial) ? warm->P.p : nullptr;
   if (!wp && C->in_solve && C->plast_valid) wp = C->Plast.p;
+  // Second candidate: the slot's own previous basis.  R(w~) starts from the current iterate's
+  // basis; after a rejected Newton step the next trial point lies near the last one, whose basis
+  // this slot still holds, so it refines where the iterate's basis is too far off.
+  const double* wp2 =
+      (C->in_solve && &e != warm && e.valid && !e.trivial && e.P.p != wp) ? e.P.p : nullptr;
   // Mixed form: a refinement whose correction is <= 1e-6 leaves a basis accurate to ~1e-12,
   // below the accuracy of its emulated products; the eigenvalues (Rayleigh quotients, which decide
   // alpha and Omega) are accurate to second order.  The FP64 form refines to FP64 rounding.
   C->jw.refine_done = C->opt.precision == KOT_MIXED ? 1e-6 : 1e-8;
   C->eig_sweeps += eig_sym_f64(C->st, l, Z, wp, e.P.p, e.sig.p, C->jw, kMaxSweeps, C->hs,
-                               C->opt.eig_ctas, C->opt.eig_refine);
+                               C->opt.eig_ctas, C->opt.eig_refine, wp2);
   C->eig_calls += 1;
   C->eig_refined += C->jw.last_refine > 0;
   C->eig_refine_steps += C->jw.last_refine;

@@ -298,13 +298,14 @@ struct JacobiWork {
 // symmetric, read only).  If warm != nullptr its columns (an orthogonal l x l basis, row-major)
 // are used as the starting basis.  P: l x l output (row-major, column j = eigenvector j).
 // With a warm basis the decomposition is first refined from it (at most max_refine steps of
-// the Ogita-Aishima iteration, GEMMs only); if that does not converge quickly it is rebuilt by
-// Jacobi sweeps from the same basis.  w.last_sweeps / w.last_refine report which ran.
+// the Ogita-Aishima iteration, GEMMs only); if that does not converge quickly, from warm2 (an
+// alternative basis, may alias P) when given, and failing both it is rebuilt by Jacobi sweeps
+// from warm.  w.last_sweeps / w.last_refine report which ran.
 // Returns the number of sweeps taken; throws on non-convergence within max_sweeps.
 // ctas: CTAs of the cooperative launch (0 = one per SM).
 int eig_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, double* P,
                 double* sig, JacobiWork& w, int max_sweeps, double* host_scal, int ctas,
-                int max_refine);
+                int max_refine, const double* warm2 = nullptr);
 
 // ------------------------------------------------------------------ tensor cores (tc_gemm.cu)
 // Logical operand of C = alpha op(A) op(B)^T + beta C: element (r, k) is
