@@ -511,8 +511,10 @@ int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
   const size_t L2 = (size_t)l * l;
   // FP64 pipes: five products per step, the two symmetric ones on their upper halves only.
   // Emulated FP64 (w.oz): the basis X sits in the right half of an l x 2l buffer whose left half
-  // receives Z X, so that X^T [Z X | X] gives S and G in one product (launches, not flops, are
-  // what a step costs at moderate l).
+  // holds Y = Z X, so that X^T [Y | X] gives S and G in one product (launches, not flops, are
+  // what a step costs at moderate l).  Read as 2l x l rows, the buffer interleaves the rows of Y
+  // and X, so one product [Y | X] (I + E) both updates the basis and carries Y = Z X to it: only
+  // the first step multiplies by Z, each step after it takes two products.
   const bool merged = w.oz != nullptr;
   const int ldx = merged ? 2 * l : l;
   for (DevBuf<double>* b : {&w.Xa, &w.Xb, &w.S}) b->alloc(merged ? 2 * L2 : L2);
@@ -537,7 +539,7 @@ int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
     if (merged) {
       double* B = (k & 1) ? w.Xb.p : w.Xa.p;            // [Z X | X], X = B + l
       Xn = ((k & 1) ? w.Xa.p : w.Xb.p) + l;
-      gemm_acc(st, w.oz, false, false, l, l, l, 1.0, Z, l, X, ldX, nullptr, 0.0, B, ldx, 0);     // Z X
+      if (k == 0) gemm_acc(st, w.oz, false, false, l, l, l, 1.0, Z, l, X, ldX, nullptr, 0.0, B, ldx, 0);
       gemm_acc(st, w.oz, true, false, l, 2 * l, l, 1.0, X, ldX, B, ldx, nullptr, 0.0, w.S.p, ldx, 0);
       S = w.S.p;                                          // X^T Z X
       G = w.S.p + l;                                      // X^T X
@@ -558,7 +560,10 @@ int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
       KOT_CHECK_LAUNCH();
       KOT_LAUNCHED(1);
     }
-    gemm_acc(st, w.oz, false, false, l, l, l, 1.0, X, ldX, w.F.p, l, nullptr, 0.0, Xn, ldx, 0);   // X (I + E)
+    if (merged)   // [Y | X] (I + E): rows (Y_i, X_i) of the buffer as 2l rows of length l
+      gemm_acc(st, w.oz, false, false, 2 * l, l, l, 1.0, X - l, l, w.F.p, l, nullptr, 0.0, Xn - l, l, 0);
+    else
+      gemm_acc(st, w.oz, false, false, l, l, l, 1.0, X, ldX, w.F.p, l, nullptr, 0.0, Xn, ldx, 0);   // X (I + E)
     unsigned long long hm[2] = {0, 0};
     KOT_CUDA(cudaMemcpyAsync(hm, w.mx.p, sizeof(hm), cudaMemcpyDeviceToHost, st));
     KOT_CUDA(cudaStreamSynchronize(st));
