@@ -136,6 +136,7 @@ __global__ void k_refine_correction(int l, int ld, const double* __restrict__ S,
       f = 1.0 + 0.5 * (1.0 - g);
       r_abs = fabs(1.0 - g);
       lam[j] = lj;
+      if (lj <= 0.0) atomicAdd(mx + 2, 1ull);   // |alpha-bar| if this step is the last
     } else {
       const double li = lrow[threadIdx.y];
       f = (S[ij] - lj * g) / (lj - li);
@@ -521,7 +522,7 @@ int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
   for (DevBuf<double>* b : {&w.Y, &w.G, &w.F}) b->alloc(L2);
   w.lam.alloc((size_t)l);
   w.rank.alloc((size_t)l);
-  w.mx.alloc(2);
+  w.mx.alloc(3);
   const dim3 g2(cdiv(l, 32), cdiv(l, 8)), b2(32, 8);
   const double* X = warm;
   int ldX = l;
@@ -553,7 +554,7 @@ int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
       G = w.G.p;
       lds = l;
     }
-    KOT_CUDA(cudaMemsetAsync(w.mx.p, 0, 2 * sizeof(unsigned long long), st));
+    KOT_CUDA(cudaMemsetAsync(w.mx.p, 0, 3 * sizeof(unsigned long long), st));
     {
       ProfScope ps(st, KC_REFINE, 12.0 * (double)L2, 8.0 * 3.0 * (double)L2);
       launch_pdl(k_refine_correction, dim3(g2), dim3(b2), 0, st, l, lds, S, G, w.F.p, w.lam.p, w.mx.p);
@@ -564,7 +565,7 @@ int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
       gemm_acc(st, w.oz, false, false, 2 * l, l, l, 1.0, X - l, l, w.F.p, l, nullptr, 0.0, Xn - l, l, 0);
     else
       gemm_acc(st, w.oz, false, false, l, l, l, 1.0, X, ldX, w.F.p, l, nullptr, 0.0, Xn, ldx, 0);   // X (I + E)
-    unsigned long long hm[2] = {0, 0};
+    unsigned long long hm[3] = {0, 0, 0};
     KOT_CUDA(cudaMemcpyAsync(hm, w.mx.p, sizeof(hm), cudaMemcpyDeviceToHost, st));
     KOT_CUDA(cudaStreamSynchronize(st));
     double me, mr;
@@ -580,6 +581,7 @@ int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
       k_gather_vec<<<g2, b2, 0, st>>>(l, w.lam.p, X, ldX, w.rank.p, P, sig);
       KOT_CHECK_LAUNCH();
       KOT_LAUNCHED(2);
+      w.last_nb = (int)hm[2];
       return k + 1;
     }
   }
@@ -593,6 +595,7 @@ int eig_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, dou
                 int max_refine, const double* warm2) {
   w.last_sweeps = 0;
   w.last_refine = 0;
+  w.last_nb = -1;
   if (max_refine > 0) {
     for (const double* start : {warm, warm2}) {
       if (!start) continue;

@@ -263,10 +263,14 @@ void eig_into(kot_ctx* C, const double* Z, EigSlot& e, const EigSlot* warm) {
   C->eig_calls += 1;
   C->eig_refined += C->jw.last_refine > 0;
   C->eig_refine_steps += C->jw.last_refine;
-  count_nonpos(C->st, l, e.sig.p, C->iscal.p);
-  KOT_CUDA(cudaMemcpyAsync(C->hi, C->iscal.p, sizeof(int), cudaMemcpyDeviceToHost, C->st));
-  KOT_CUDA(cudaStreamSynchronize(C->st));
-  e.nb = C->hi[0];
+  if (C->jw.last_nb >= 0) {
+    e.nb = C->jw.last_nb;   // counted by the refinement's last step, read with its convergence test
+  } else {
+    count_nonpos(C->st, l, e.sig.p, C->iscal.p);
+    KOT_CUDA(cudaMemcpyAsync(C->hi, C->iscal.p, sizeof(int), cudaMemcpyDeviceToHost, C->st));
+    KOT_CUDA(cudaStreamSynchronize(C->st));
+    e.nb = C->hi[0];
+  }
   e.valid = true;
   e.trivial = wp == nullptr && C->jw.last_sweeps == 0 && C->jw.last_refine == 0;
   if (C->in_solve && !e.trivial) {
@@ -302,8 +306,17 @@ void proj_into(kot_ctx* C, const double* X, const double* S, double a, double c,
 // R(w) of Eq. (4.2) into r; eigen-decomposition of Z(w) into e.
 // save_fv: (gamma, X) is the EG iterate v; keep F(v) = (r1, Phi*(gamma) + lambda1 I) for the next
 // extragradient step, which starts by evaluating exactly these (same kernels, same bits).
+// defer: leave |r1|^2, |r2|^2 in scal[0..1] unread (the caller fetches them together with its
+// own scalars and calls finish_residual).
+void finish_residual(kot_ctx* C, ResState& r) {
+  r.n1 = std::sqrt(C->hs[0]);
+  r.n2 = std::sqrt(C->hs[1]);
+  r.norm = r.n1 + r.n2;
+  if (!std::isfinite(r.norm)) fail(KOT_ERR_NONFINITE, "residual is not finite");
+}
+
 void residual(kot_ctx* C, const double* gamma, const double* X, EigSlot& e, const EigSlot* warm,
-              ResState& r, bool save_fv = false) {
+              ResState& r, bool save_fv = false, bool defer = false) {
   Range range("kot/residual");
   const int l = C->l;
   const size_t L2 = (size_t)l * l;
@@ -319,11 +332,9 @@ void residual(kot_ctx* C, const double* gamma, const double* X, EigSlot& e, cons
   }
   // r2 = X - Pi(Z) with |r1|^2 and |r2|^2 in one pass
   sub_norms(C->st, l, r.r1.p, L2, X, C->M2.p, r.r2.p, C->scal.p, C->partial.p);
+  if (defer) return;
   fetch(C, 2);
-  r.n1 = std::sqrt(C->hs[0]);
-  r.n2 = std::sqrt(C->hs[1]);
-  r.norm = r.n1 + r.n2;
-  if (!std::isfinite(r.norm)) fail(KOT_ERR_NONFINITE, "residual is not finite");
+  finish_residual(C, r);
 }
 
 // out = T_k[S] (Sec. 4.3) with the eigen-decomposition in e and regularisation mu.
@@ -709,14 +720,14 @@ void eg_step(kot_ctx* C, double eta) {
   C->fv_valid = false;                                            // v has moved
 }
 
-double pair_inner(kot_ctx* C, const ResState& r, const double* dg, const double* dX) {
+// <R(w~), dw> into scal[2] + scal[3] and |dg|^2, |dX|^2 into scal[4], scal[5] (read with the
+// deferred residual of w~ in one fetch)
+void pair_inner(kot_ctx* C, const ResState& r, const double* dg, const double* dX) {
   const int l = C->l;
-  dot_f64(C->st, l, r.r1.p, dg, C->scal.p, C->partial.p);
-  dot_f64(C->st, l * l, r.r2.p, dX, C->scal.p + 1, C->partial.p);
-  sumsq_f64(C->st, l, dg, C->scal.p + 2, C->partial.p);
-  sumsq_f64(C->st, (size_t)l * l, dX, C->scal.p + 3, C->partial.p);
-  fetch(C, 4);
-  return C->hs[0] + C->hs[1];
+  dot_f64(C->st, l, r.r1.p, dg, C->scal.p + 2, C->partial.p);
+  dot_f64(C->st, l * l, r.r2.p, dX, C->scal.p + 3, C->partial.p);
+  sumsq_f64(C->st, l, dg, C->scal.p + 4, C->partial.p);
+  sumsq_f64(C->st, (size_t)l * l, dX, C->scal.p + 5, C->partial.p);
 }
 
 void swap_slots(EigSlot& a, EigSlot& b) {
@@ -1159,9 +1170,12 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
       cgt += cgk;
       axpby(st, l, 1.0, C->g.p, 1.0, C->dg.p, C->tg.p);
       axpby(st, L2, 1.0, C->X.p, 1.0, C->dX.p, C->tX.p);
-      residual(C, C->tg.p, C->tX.p, C->et, &C->ew, C->rt);
-      const double inner = pair_inner(C, C->rt, C->dg.p, C->dX.p);
-      const double dwn = std::sqrt(C->hs[2]) + std::sqrt(C->hs[3]);
+      residual(C, C->tg.p, C->tX.p, C->et, &C->ew, C->rt, false, true);
+      pair_inner(C, C->rt, C->dg.p, C->dX.p);
+      fetch(C, 6);
+      finish_residual(C, C->rt);
+      const double inner = C->hs[2] + C->hs[3];
+      const double dwn = std::sqrt(C->hs[4]) + std::sqrt(C->hs[5]);
       const double rho = -inner;
       if (rho >= o.alpha2 * dwn * dwn) theta = std::max(o.theta_min, o.beta0 * theta);
       else if (rho >= o.alpha1 * dwn * dwn) theta = o.beta1 * theta;

@@ -280,10 +280,11 @@ struct JacobiWork {
   DevBuf<int> flags;        // [error, 2 * sweeps + final buffer]
   // refinement of a warm basis (l x l each, ld l): ping-pong bases, Z X, X^T Z X, X^T X, I + E
   DevBuf<double> Xa, Xb, Y, S, G, F, lam;
-  DevBuf<unsigned long long> mx;   // [max |E_ij| (i != j), max |I - X^T X|] as ordered bits
+  DevBuf<unsigned long long> mx;   // [max |E_ij| (i != j), max |I - X^T X|] as ordered bits, count of lambda <= 0
   int threads_override = 0;        // > 0: threads per CTA of the Jacobi kernel (the autotuner's probes)
   int last_sweeps = 0;             // Jacobi sweeps of the last call
   int last_refine = 0;             // refinement steps of the last call (0: Jacobi was used)
+  int last_nb = -1;                // eigenvalues <= 0 of a refined decomposition (-1: not counted)
   void release() {
     for (DevBuf<double>* b : {&A, &V, &rot, &partial, &scal, &Xa, &Xb, &Y, &S, &G, &F, &lam}) b->release();
     pairs.release();
