@@ -212,6 +212,9 @@ bool mixed(const kot_ctx* C) { return C->opt.precision == KOT_MIXED && !C->force
 // i.e. the six BF16 x BF16 products (FP32 accumulation) of a three-term split, about FP32
 // accuracy; the FP64-accuracy products of the mixed form use oz.slices (six).
 constexpr int kCgSlices = 3;
+// Device scalar slot of the EG iterate's |r1|^2, |r2|^2 while their readback waits for the trial
+// point's (clear of the slots the Newton direction and the theta rule use).
+constexpr int kRvSlot = 24;
 
 void phi_star_nd(kot_ctx* C, const double* gamma, double* out) {
   if (!mixed(C)) return phi_star(C, gamma, out);
@@ -306,17 +309,17 @@ void proj_into(kot_ctx* C, const double* X, const double* S, double a, double c,
 // R(w) of Eq. (4.2) into r; eigen-decomposition of Z(w) into e.
 // save_fv: (gamma, X) is the EG iterate v; keep F(v) = (r1, Phi*(gamma) + lambda1 I) for the next
 // extragradient step, which starts by evaluating exactly these (same kernels, same bits).
-// defer: leave |r1|^2, |r2|^2 in scal[0..1] unread (the caller fetches them together with its
-// own scalars and calls finish_residual).
-void finish_residual(kot_ctx* C, ResState& r) {
-  r.n1 = std::sqrt(C->hs[0]);
-  r.n2 = std::sqrt(C->hs[1]);
+// defer: leave |r1|^2, |r2|^2 in scal[slot], scal[slot + 1] unread (the caller fetches them
+// together with its own scalars and calls finish_residual).
+void finish_residual(kot_ctx* C, ResState& r, int slot = 0) {
+  r.n1 = std::sqrt(C->hs[slot]);
+  r.n2 = std::sqrt(C->hs[slot + 1]);
   r.norm = r.n1 + r.n2;
   if (!std::isfinite(r.norm)) fail(KOT_ERR_NONFINITE, "residual is not finite");
 }
 
 void residual(kot_ctx* C, const double* gamma, const double* X, EigSlot& e, const EigSlot* warm,
-              ResState& r, bool save_fv = false, bool defer = false) {
+              ResState& r, bool save_fv = false, bool defer = false, int slot = 0) {
   Range range("kot/residual");
   const int l = C->l;
   const size_t L2 = (size_t)l * l;
@@ -331,7 +334,7 @@ void residual(kot_ctx* C, const double* gamma, const double* X, EigSlot& e, cons
     C->fv_valid = true;                                       // F_gamma(v) = r1(v)
   }
   // r2 = X - Pi(Z) with |r1|^2 and |r2|^2 in one pass
-  sub_norms(C->st, l, r.r1.p, L2, X, C->M2.p, r.r2.p, C->scal.p, C->partial.p);
+  sub_norms(C->st, l, r.r1.p, L2, X, C->M2.p, r.r2.p, C->scal.p + slot, C->partial.p);
   if (defer) return;
   fetch(C, 2);
   finish_residual(C, r);
@@ -1161,7 +1164,8 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
     while (C->rw.norm > tol && it < o.max_iter) {
       if (o.use_eg) {
         eg_step(C, eta);
-        residual(C, C->vg.p, C->vX.p, C->ev, &C->ev, C->rv, true);
+        // |R(v)| is needed only by the acceptance test: read with the trial point's norms
+        residual(C, C->vg.p, C->vX.p, C->ev, &C->ev, C->rv, true, true, kRvSlot);
       }
       const double mu = theta * C->rw.norm;
       // mixed form: tensor-core products far from the solution, FP64 near it
@@ -1172,8 +1176,9 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
       axpby(st, L2, 1.0, C->X.p, 1.0, C->dX.p, C->tX.p);
       residual(C, C->tg.p, C->tX.p, C->et, &C->ew, C->rt, false, true);
       pair_inner(C, C->rt, C->dg.p, C->dX.p);
-      fetch(C, 6);
+      fetch(C, o.use_eg ? kRvSlot + 2 : 6);
       finish_residual(C, C->rt);
+      if (o.use_eg) finish_residual(C, C->rv, kRvSlot);
       const double inner = C->hs[2] + C->hs[3];
       const double dwn = std::sqrt(C->hs[4]) + std::sqrt(C->hs[5]);
       const double rho = -inner;
