@@ -35,18 +35,25 @@ cudaEvent_t Profiler::get_event() {
 }
 
 void Profiler::begin(cudaStream_t st, int cls, cudaEvent_t* a) {
+  std::lock_guard<std::mutex> lk(mu);
   *a = get_event();
   KOT_CUDA(cudaEventRecord(*a, st));
 }
 
 void Profiler::end(cudaStream_t st, int cls, cudaEvent_t a, double fl, double by, double ex) {
+  std::lock_guard<std::mutex> lk(mu);
   cudaEvent_t b = get_event();
   if (cudaEventRecord(b, st) != cudaSuccess) return;
   pending.push_back({cls, a, b, fl, by, ex});
-  if (pending.size() > 4096) collect();
+  if (pending.size() > 4096) collect_locked();
 }
 
 void Profiler::collect() {
+  std::lock_guard<std::mutex> lk(mu);
+  collect_locked();
+}
+
+void Profiler::collect_locked() {
   for (auto& q : pending) {
     float t = 0.f;
     if (cudaEventSynchronize(q.b) == cudaSuccess && cudaEventElapsedTime(&t, q.a, q.b) == cudaSuccess) {
@@ -63,12 +70,14 @@ void Profiler::collect() {
 }
 
 void Profiler::reset() {
-  collect();
+  std::lock_guard<std::mutex> lk(mu);
+  collect_locked();
   for (int i = 0; i < KC_COUNT; ++i) launches[i] = seen[i] = 0, ms[i] = flops[i] = bytes[i] = exec[i] = 0.0;
 }
 
 void Profiler::release() {
-  collect();
+  std::lock_guard<std::mutex> lk(mu);
+  collect_locked();
   for (auto e : pool) cudaEventDestroy(e);
   pool.clear();
 }

@@ -8,6 +8,9 @@
 #include <cstring>
 #include <functional>
 #include <atomic>
+#include <condition_variable>
+#include <exception>
+#include <mutex>
 #include <numeric>
 #include <thread>
 #include <string>
@@ -101,6 +104,19 @@ struct kot_ctx {
   std::vector<double> trace;   // per iteration: ||R||, mu, CG steps, theta, direction kind
   int last_dir_kind = 0;       // 0 FP64, 1 tensor cores, 2 tensor cores + FP64 refinement
   Profiler prof;
+  // Algorithm 2's extragradient sequence v runs beside the Newton step on w (they meet only in
+  // the acceptance test): its own context (buffers, stream, workspaces) driven by a helper
+  // host thread, so that one sequence's readbacks overlap the other's GPU work.
+  kot_ctx* lane = nullptr;
+  kot_ctx* owner = nullptr;          // set in the lane: the context whose profiler it shares
+  std::thread lane_thread;
+  std::mutex lane_mu;
+  std::condition_variable lane_cv;
+  int lane_job = 0;                  // 0 idle, 1 run one EG step and R(v), 2 quit
+  bool lane_busy = false;
+  double lane_eta = 0.0;
+  std::exception_ptr lane_err;
+  cudaEvent_t lane_ev = nullptr;     // this context's reads of the lane's buffers, awaited by the lane
 };
 
 namespace {
@@ -212,9 +228,6 @@ bool mixed(const kot_ctx* C) { return C->opt.precision == KOT_MIXED && !C->force
 // i.e. the six BF16 x BF16 products (FP32 accumulation) of a three-term split, about FP32
 // accuracy; the FP64-accuracy products of the mixed form use oz.slices (six).
 constexpr int kCgSlices = 3;
-// Device scalar slot of the EG iterate's |r1|^2, |r2|^2 while their readback waits for the trial
-// point's (clear of the slots the Newton direction and the theta rule use).
-constexpr int kRvSlot = 24;
 
 void phi_star_nd(kot_ctx* C, const double* gamma, double* out) {
   if (!mixed(C)) return phi_star(C, gamma, out);
@@ -309,17 +322,17 @@ void proj_into(kot_ctx* C, const double* X, const double* S, double a, double c,
 // R(w) of Eq. (4.2) into r; eigen-decomposition of Z(w) into e.
 // save_fv: (gamma, X) is the EG iterate v; keep F(v) = (r1, Phi*(gamma) + lambda1 I) for the next
 // extragradient step, which starts by evaluating exactly these (same kernels, same bits).
-// defer: leave |r1|^2, |r2|^2 in scal[slot], scal[slot + 1] unread (the caller fetches them
-// together with its own scalars and calls finish_residual).
-void finish_residual(kot_ctx* C, ResState& r, int slot = 0) {
-  r.n1 = std::sqrt(C->hs[slot]);
-  r.n2 = std::sqrt(C->hs[slot + 1]);
+// defer: leave |r1|^2, |r2|^2 in scal[0..1] unread (the caller fetches them together with its
+// own scalars and calls finish_residual).
+void finish_residual(kot_ctx* C, ResState& r) {
+  r.n1 = std::sqrt(C->hs[0]);
+  r.n2 = std::sqrt(C->hs[1]);
   r.norm = r.n1 + r.n2;
   if (!std::isfinite(r.norm)) fail(KOT_ERR_NONFINITE, "residual is not finite");
 }
 
 void residual(kot_ctx* C, const double* gamma, const double* X, EigSlot& e, const EigSlot* warm,
-              ResState& r, bool save_fv = false, bool defer = false, int slot = 0) {
+              ResState& r, bool save_fv = false, bool defer = false) {
   Range range("kot/residual");
   const int l = C->l;
   const size_t L2 = (size_t)l * l;
@@ -334,7 +347,7 @@ void residual(kot_ctx* C, const double* gamma, const double* X, EigSlot& e, cons
     C->fv_valid = true;                                       // F_gamma(v) = r1(v)
   }
   // r2 = X - Pi(Z) with |r1|^2 and |r2|^2 in one pass
-  sub_norms(C->st, l, r.r1.p, L2, X, C->M2.p, r.r2.p, C->scal.p + slot, C->partial.p);
+  sub_norms(C->st, l, r.r1.p, L2, X, C->M2.p, r.r2.p, C->scal.p, C->partial.p);
   if (defer) return;
   fetch(C, 2);
   finish_residual(C, r);
@@ -799,6 +812,117 @@ void reset_slots(kot_ctx* C) {
   C->plast_valid = false;
 }
 
+// ------------------------------------------------------------------ the EG lane
+// The helper thread of a lane context L (L->owner = the solving context O): waits for a job, runs
+// one extragradient step on L's iterate v and evaluates R(v) (its last readback leaves L's
+// stream idle), reports completion or the error.
+void lane_work(kot_ctx* L) {
+  kot_ctx* O = L->owner;
+  for (;;) {
+    double eta = 0.0;
+    {
+      std::unique_lock<std::mutex> lk(O->lane_mu);
+      O->lane_cv.wait(lk, [&] { return O->lane_job != 0; });
+      if (O->lane_job == 2) return;
+      eta = O->lane_eta;
+    }
+    std::exception_ptr err;
+    try {
+      KOT_CUDA(cudaSetDevice(L->opt.device));
+      set_current_profiler(O->prof.mask ? &O->prof : nullptr);
+      KOT_CUDA(cudaStreamWaitEvent(L->st, O->lane_ev, 0));   // O's copies out of L's buffers
+      eg_step(L, eta);
+      residual(L, L->vg.p, L->vX.p, L->ev, &L->ev, L->rv, true);
+    } catch (...) {
+      err = std::current_exception();
+    }
+    set_current_profiler(nullptr);
+    {
+      std::lock_guard<std::mutex> lk(O->lane_mu);
+      O->lane_err = err;
+      O->lane_job = 0;
+      O->lane_busy = false;
+    }
+    O->lane_cv.notify_all();
+  }
+}
+
+void lane_start(kot_ctx* C, double eta) {
+  {
+    std::lock_guard<std::mutex> lk(C->lane_mu);
+    C->lane_eta = eta;
+    C->lane_err = nullptr;
+    C->lane_busy = true;
+    C->lane_job = 1;
+  }
+  C->lane_cv.notify_all();
+}
+
+// Wait for the lane's step; rethrow its error.
+void lane_wait(kot_ctx* C) {
+  std::unique_lock<std::mutex> lk(C->lane_mu);
+  C->lane_cv.wait(lk, [&] { return !C->lane_busy; });
+  std::exception_ptr e = C->lane_err;
+  C->lane_err = nullptr;
+  lk.unlock();
+  if (e) std::rethrow_exception(e);
+}
+
+// Leaves no lane step running when the solving thread unwinds.
+struct LaneJoin {
+  kot_ctx* C = nullptr;
+  ~LaneJoin() {
+    if (!C) return;
+    std::unique_lock<std::mutex> lk(C->lane_mu);
+    C->lane_cv.wait(lk, [&] { return !C->lane_busy; });
+    C->lane_err = nullptr;
+  }
+};
+
+// The lane context of C (created on first use: own stream, pinned scalars, helper thread), set up
+// for the current features: R, Q, z copied in, iterate v = w, slots and counters reset.
+kot_ctx* lane_for_solve(kot_ctx* C) {
+  if (!C->lane) {
+    kot_ctx* L = new kot_ctx();
+    L->opt = C->opt;
+    L->opt.stream = nullptr;
+    L->owner = C;
+    try {
+      KOT_CUDA(cudaStreamCreateWithFlags(&L->st, cudaStreamNonBlocking));
+      L->own_stream = true;
+      KOT_CUDA(cudaMallocHost(&L->hs, 64 * sizeof(double)));
+      KOT_CUDA(cudaMallocHost(&L->hi, 16 * sizeof(int)));
+      if (!C->lane_ev) KOT_CUDA(cudaEventCreateWithFlags(&C->lane_ev, cudaEventDisableTiming));
+    } catch (...) {
+      kot_destroy(L);
+      throw;
+    }
+    C->lane = L;
+    C->lane_thread = std::thread(lane_work, L);
+  }
+  kot_ctx* L = C->lane;
+  const int l = C->l;
+  const size_t L2 = (size_t)l * l;
+  L->l = l;
+  ensure(L, l);
+  L->lambda1 = C->lambda1;
+  L->lambda2 = C->lambda2;
+  L->jw.oz = L->opt.precision == KOT_MIXED ? &L->oz : nullptr;
+  L->oz.f64_below = L->opt.tc_min_flops;
+  L->force64 = false;
+  reset_slots(L);
+  L->in_solve = true;
+  L->eig_calls = L->eig_sweeps = L->eig_refined = L->eig_refine_steps = 0;
+  cudaStream_t st = C->st;
+  KOT_CUDA(cudaMemcpyAsync(L->R.p, C->R.p, L2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  KOT_CUDA(cudaMemcpyAsync(L->Q.p, C->Q.p, L2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  KOT_CUDA(cudaMemcpyAsync(L->z.p, C->z.p, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  KOT_CUDA(cudaMemcpyAsync(L->vg.p, C->g.p, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  KOT_CUDA(cudaMemcpyAsync(L->vX.p, C->X.p, L2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  KOT_CUDA(cudaEventRecord(C->lane_ev, st));
+  return L;
+}
+
 }  // namespace
 
 // ================================================================== C ABI
@@ -818,6 +942,8 @@ kot_status run(kot_ctx* C, const std::function<void()>& body) {
   try {
     body();
     if (C && C->opt.precision == KOT_MIXED && gemm_oz_error(C->st, C->oz))
+      fail(KOT_ERR_TIMEOUT, "tensor-core FP64-emulation wait timed out");
+    if (C && C->lane && C->opt.precision == KOT_MIXED && gemm_oz_error(C->lane->st, C->lane->oz))
       fail(KOT_ERR_TIMEOUT, "tensor-core FP64-emulation wait timed out");
     return KOT_OK;
   } catch (const Error& e) {
@@ -881,6 +1007,17 @@ kot_status kot_create(kot_ctx** out, const kot_options* opt) {
 kot_status kot_destroy(kot_ctx* C) {
   if (!C) return KOT_OK;
   cudaSetDevice(C->opt.device);
+  if (C->lane) {
+    {
+      std::lock_guard<std::mutex> lk(C->lane_mu);
+      C->lane_job = 2;
+    }
+    C->lane_cv.notify_all();
+    if (C->lane_thread.joinable()) C->lane_thread.join();
+    kot_destroy(C->lane);
+    C->lane = nullptr;
+  }
+  if (C->lane_ev) cudaEventDestroy(C->lane_ev);
   if (C->st) cudaStreamSynchronize(C->st);
   for (DevBuf<double>* b : {&C->Q, &C->K, &C->R, &C->z, &C->w_mu, &C->w_nu, &C->c, &C->g, &C->X,
                             &C->vg, &C->vX, &C->tg, &C->tX, &C->dg, &C->dX, &C->M1, &C->M2,
@@ -1160,12 +1297,14 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
     C->hist.clear();
     C->trace.clear();
     if (o.record_history) C->hist.push_back(C->rw.norm);
+    // the EG sequence v (its own context, stream and helper thread) from v0 = w0
+    kot_ctx* V = o.use_eg ? lane_for_solve(C) : nullptr;
     int it = 0, acc = 0, egt = 0, cgt = 0;
     while (C->rw.norm > tol && it < o.max_iter) {
-      if (o.use_eg) {
-        eg_step(C, eta);
-        // |R(v)| is needed only by the acceptance test: read with the trial point's norms
-        residual(C, C->vg.p, C->vX.p, C->ev, &C->ev, C->rv, true, true, kRvSlot);
+      LaneJoin join;
+      if (V) {
+        lane_start(C, eta);   // one EG step on v and R(v), beside the Newton step below
+        join.C = C;
       }
       const double mu = theta * C->rw.norm;
       // mixed form: tensor-core products far from the solution, FP64 near it
@@ -1176,32 +1315,40 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
       axpby(st, L2, 1.0, C->X.p, 1.0, C->dX.p, C->tX.p);
       residual(C, C->tg.p, C->tX.p, C->et, &C->ew, C->rt, false, true);
       pair_inner(C, C->rt, C->dg.p, C->dX.p);
-      fetch(C, o.use_eg ? kRvSlot + 2 : 6);
+      fetch(C, 6);
       finish_residual(C, C->rt);
-      if (o.use_eg) finish_residual(C, C->rv, kRvSlot);
+      if (V) {
+        join.C = nullptr;
+        lane_wait(C);
+      }
       const double inner = C->hs[2] + C->hs[3];
       const double dwn = std::sqrt(C->hs[4]) + std::sqrt(C->hs[5]);
       const double rho = -inner;
       if (rho >= o.alpha2 * dwn * dwn) theta = std::max(o.theta_min, o.beta0 * theta);
       else if (rho >= o.alpha1 * dwn * dwn) theta = o.beta1 * theta;
       else theta = std::min(o.theta_max, o.beta2 * theta);
-      if (!o.use_eg || C->rt.norm <= C->rv.norm) {
+      if (!V || C->rt.norm <= V->rv.norm) {
         std::swap(C->g, C->tg);
         std::swap(C->X, C->tX);
         swap_res(C->rw, C->rt);
         swap_slots(C->ew, C->et);
         ++acc;
       } else {
-        KOT_CUDA(cudaMemcpyAsync(C->g.p, C->vg.p, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        KOT_CUDA(cudaMemcpyAsync(C->X.p, C->vX.p, L2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        swap_res(C->rw, C->rv);
-        swap_slots(C->ew, C->ev);
-        // the EG sequence keeps its own basis: copy it back for the next R(v) warm start
-        KOT_CUDA(cudaMemcpyAsync(C->ev.P.p, C->ew.P.p, L2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        KOT_CUDA(cudaMemcpyAsync(C->ev.sig.p, C->ew.sig.p, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        C->ev.nb = C->ew.nb;
-        C->ev.valid = true;
-        C->ev.trivial = C->ew.trivial;
+        // w = v: the iterate, its residual and its eigen-decomposition copied out of the lane
+        // (whose stream is idle after R(v)); the lane's next step waits for these reads
+        KOT_CUDA(cudaMemcpyAsync(C->g.p, V->vg.p, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        KOT_CUDA(cudaMemcpyAsync(C->X.p, V->vX.p, L2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        KOT_CUDA(cudaMemcpyAsync(C->rw.r1.p, V->rv.r1.p, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        KOT_CUDA(cudaMemcpyAsync(C->rw.r2.p, V->rv.r2.p, L2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        C->rw.n1 = V->rv.n1;
+        C->rw.n2 = V->rv.n2;
+        C->rw.norm = V->rv.norm;
+        KOT_CUDA(cudaMemcpyAsync(C->ew.P.p, V->ev.P.p, L2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        KOT_CUDA(cudaMemcpyAsync(C->ew.sig.p, V->ev.sig.p, l * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        C->ew.nb = V->ev.nb;
+        C->ew.valid = V->ev.valid;
+        C->ew.trivial = V->ev.trivial;
+        KOT_CUDA(cudaEventRecord(C->lane_ev, st));
         ++egt;
       }
       ++it;
@@ -1230,6 +1377,12 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
     R.eig_sweeps = (int)C->eig_sweeps;
     R.eig_refined = (int)C->eig_refined;
     R.eig_refine_steps = (int)C->eig_refine_steps;
+    if (V) {
+      R.eig_calls += (int)V->eig_calls;
+      R.eig_sweeps += (int)V->eig_sweeps;
+      R.eig_refined += (int)V->eig_refined;
+      R.eig_refine_steps += (int)V->eig_refine_steps;
+    }
   });
   if (s == KOT_OK && !converged) {
     s = KOT_ERR_NO_CONVERGENCE;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -101,15 +102,21 @@ struct Profiler {
   std::vector<cudaEvent_t> pool;
   long launches[KC_COUNT] = {};
   double ms[KC_COUNT] = {}, flops[KC_COUNT] = {}, bytes[KC_COUNT] = {}, exec[KC_COUNT] = {};
+  std::mutex mu;                       // the solver's two host threads share one profiler
   bool on(int cls) const { return (mask >> cls) & 1; }
   // enabled, and this launch is one of the sampled ones
-  bool take(int cls) { return on(cls) && (seen[cls]++ % every) == 0; }
+  bool take(int cls) {
+    std::lock_guard<std::mutex> lk(mu);
+    return on(cls) && (seen[cls]++ % every) == 0;
+  }
   cudaEvent_t get_event();
   void begin(cudaStream_t st, int cls, cudaEvent_t* a);
   void end(cudaStream_t st, int cls, cudaEvent_t a, double fl, double by, double ex);
   void collect();
   void reset();
   void release();
+ private:
+  void collect_locked();
 };
 Profiler* current_profiler();
 void set_current_profiler(Profiler* p);
