@@ -1313,11 +1313,22 @@ kot_status kot_ssn_solve(kot_ctx* C, double tol, double* gamma_out, double* X_ou
       cgt += cgk;
       axpby(st, l, 1.0, C->g.p, 1.0, C->dg.p, C->tg.p);
       axpby(st, L2, 1.0, C->X.p, 1.0, C->dX.p, C->tX.p);
+      if (V && !C->plast_valid) {
+        // no basis of its own yet (w0 = 0 gives a diagonal Z): wait for the EG projections and
+        // start R(w~) from the lane's latest basis instead of cold Jacobi sweeps
+        join.C = nullptr;
+        lane_wait(C);
+        if (V->plast_valid) {
+          KOT_CUDA(cudaMemcpyAsync(C->Plast.p, V->Plast.p, L2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+          C->plast_valid = true;
+          KOT_CUDA(cudaEventRecord(C->lane_ev, st));
+        }
+      }
       residual(C, C->tg.p, C->tX.p, C->et, &C->ew, C->rt, false, true);
       pair_inner(C, C->rt, C->dg.p, C->dX.p);
       fetch(C, 6);
       finish_residual(C, C->rt);
-      if (V) {
+      if (V && join.C) {
         join.C = nullptr;
         lane_wait(C);
       }
