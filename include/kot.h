@@ -247,8 +247,9 @@ kot_status kot_bootstrap_solve(kot_ctx* ctx, int B, int n, const double* Xs, con
  * warm (may be NULL): an orthogonal l x l basis (row-major, orthonormal columns) close to the
  * eigenbasis, e.g. the one of a nearby matrix.  With it the library first refines warm into
  * the eigenbasis (Ogita-Aishima iteration, at most opt.eig_refine steps of FP64 products) and
- * rebuilds by Jacobi sweeps from warm when that does not converge; without it, Jacobi from the
- * identity.  info (host, may be NULL) receives {Jacobi sweeps, refinement steps} of the call.
+ * rebuilds by Jacobi sweeps from warm when that does not converge; without it, the same from
+ * the identity (a nearly diagonal Z then needs no sweeps).  info (host, may be NULL) receives
+ * {Jacobi sweeps, refinement steps} of the call.
  * Pointers follow the context's pointer mode.  No features are needed.  KOT_ERR_TIMEOUT if a
  * bounded wait of the cooperative Jacobi kernel gave up, KOT_ERR_NO_CONVERGENCE if the sweeps
  * did not converge. */

@@ -597,7 +597,20 @@ int eig_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, dou
   w.last_refine = 0;
   w.last_nb = -1;
   if (max_refine > 0) {
-    for (const double* start : {warm, warm2}) {
+    // No basis at all: try the identity first.  A nearly diagonal Z (the first projections of a
+    // solve when the Gram matrix K is close to diagonal, small bandwidths) refines from it in a
+    // few products, where cold Jacobi sweeps cost l - 1 grid-synchronised rounds each.
+    const double* eye = nullptr;
+    if (!warm && !warm2) {
+      if (w.eye_l != l) {
+        w.eye.alloc((size_t)l * l);
+        fill(st, (size_t)l * l, 0.0, w.eye.p);
+        add_diag(st, l, 1.0, w.eye.p, l);
+        w.eye_l = l;
+      }
+      eye = w.eye.p;
+    }
+    for (const double* start : {warm, warm2, eye}) {
       if (!start) continue;
       const int k = refine_sym_f64(st, l, Z, start, P, sig, w, max_refine);
       if (k > 0) {

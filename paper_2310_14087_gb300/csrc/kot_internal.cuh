@@ -282,6 +282,8 @@ struct JacobiWork {
   DevBuf<double> rot;       // two rounds x lp/2 pairs x (c, s)
   DevBuf<int> pairs;        // lp
   DevBuf<int> rank;         // l
+  DevBuf<double> eye;       // l x l identity, the start of a refinement without a warm basis
+  int eye_l = 0;
   DevBuf<double> partial, scal;
   DevBuf<unsigned> bar;     // grid barrier [arrivals, generation]
   DevBuf<int> flags;        // [error, 2 * sweeps + final buffer]
@@ -293,7 +295,8 @@ struct JacobiWork {
   int last_refine = 0;             // refinement steps of the last call (0: Jacobi was used)
   int last_nb = -1;                // eigenvalues <= 0 of a refined decomposition (-1: not counted)
   void release() {
-    for (DevBuf<double>* b : {&A, &V, &rot, &partial, &scal, &Xa, &Xb, &Y, &S, &G, &F, &lam}) b->release();
+    for (DevBuf<double>* b : {&A, &V, &rot, &partial, &scal, &Xa, &Xb, &Y, &S, &G, &F, &lam, &eye}) b->release();
+    eye_l = 0;
     pairs.release();
     rank.release();
     bar.release();

@@ -66,10 +66,29 @@ def check_decomposition(Z, P, sig):
 
 @pytest.mark.parametrize("l", [1, 2, 37, 64, 129, 160, 300, 512, 1024, 2048])
 def test_cold_start_jacobi(l):
+    # random eigenbasis: from l = 37 up the refinement from the identity gives up at once and
+    # Jacobi sweeps decompose; at l = 1 (already diagonal) and l = 2 the refinement may finish
     Z = clustered_symmetric(l, seed=l)
     ctx = kot.Context(device=0)
     P, sig, (sweeps, refine) = run_eig(ctx, Z)
-    assert refine == 0 and (sweeps > 0 or l == 1)
+    if l >= 37:
+        assert refine == 0 and sweeps > 0
+    else:
+        assert (refine > 0 and sweeps == 0) or (refine == 0 and sweeps > 0)
+    check_decomposition(Z, P, sig)
+
+
+@pytest.mark.parametrize("l,delta", [(50, 1e-3), (300, 1e-4), (513, 1e-5)])
+def test_cold_start_nearly_diagonal_refines_from_identity(l, delta):
+    # separated diagonal plus a small symmetric perturbation (|E| ~ delta / gap << 1): without a
+    # warm basis the refinement starts from the identity and needs no Jacobi sweep
+    rng = np.random.default_rng(5 * l)
+    d = np.linspace(-1.0, 1.0, l)[rng.permutation(l)]
+    Dm = rng.standard_normal((l, l))
+    Z = np.diag(d) + delta * 0.5 * (Dm + Dm.T) / np.sqrt(l)
+    ctx = kot.Context(device=0)
+    P, sig, (sweeps, refine) = run_eig(ctx, Z)
+    assert sweeps == 0 and 1 <= refine <= 5
     check_decomposition(Z, P, sig)
 
 
