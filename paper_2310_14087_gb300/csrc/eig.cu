@@ -508,7 +508,7 @@ constexpr double kRefineContract = 0.5;
 // Refine the warm basis into P, sig (ascending).  Returns the steps taken, or 0 if the iteration
 // gave up (P and sig are then untouched).
 int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, double* P,
-                   double* sig, JacobiWork& w, int max_steps) {
+                   double* sig, JacobiWork& w, int max_steps, double prev_me0 = 0.0) {
   const size_t L2 = (size_t)l * l;
   // FP64 pipes: five products per step, the two symmetric ones on their upper halves only.
   // Emulated FP64 (w.oz): the basis X sits in the right half of an l x 2l buffer whose left half
@@ -531,7 +531,7 @@ int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
     X = w.Xa.p + l;
     ldX = ldx;
   }
-  double prev_me = 0.0;
+  double prev_me = prev_me0;
   for (int k = 0; k < max_steps; ++k) {
     const double* S;
     const double* G;
@@ -571,7 +571,7 @@ int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
     double me, mr;
     std::memcpy(&me, &hm[0], sizeof(double));
     std::memcpy(&mr, &hm[1], sizeof(double));
-    const double cap = k == 0 ? kRefineStart : kRefineContract * prev_me;
+    const double cap = (k == 0 && prev_me <= 0.0) ? kRefineStart : kRefineContract * prev_me;
     if (!(me <= cap) || !(mr <= kRefineStart)) return 0;
     prev_me = me;
     X = Xn;
@@ -588,6 +588,57 @@ int refine_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, 
   return 0;
 }
 
+// Refinement without a warm basis, from the identity: its first step needs no product (S = Z,
+// G = I), so a Z that is diagonal to the tolerance, or too far from diagonal, costs one small
+// kernel and a readback; otherwise X = I + E continues through refine_sym_f64.  Returns the
+// steps (0: gave up); *diag = the first correction already met the tolerance (Z is diagonal,
+// the basis is the identity up to the sort).
+int refine_from_identity(cudaStream_t st, int l, const double* Z, double* P, double* sig,
+                         JacobiWork& w, int max_steps, bool* diag) {
+  *diag = false;
+  const size_t L2 = (size_t)l * l;
+  if (w.eye_l != l) {
+    w.eye.alloc(L2);
+    fill(st, L2, 0.0, w.eye.p);
+    add_diag(st, l, 1.0, w.eye.p, l);
+    w.eye_l = l;
+  }
+  w.F.alloc(L2);
+  w.lam.alloc((size_t)l);
+  w.rank.alloc((size_t)l);
+  w.mx.alloc(3);
+  KOT_CUDA(cudaMemsetAsync(w.mx.p, 0, 3 * sizeof(unsigned long long), st));
+  const dim3 g2(cdiv(l, 32), cdiv(l, 8)), b2(32, 8);
+  {
+    ProfScope ps(st, KC_REFINE, 12.0 * (double)L2, 8.0 * 3.0 * (double)L2);
+    launch_pdl(k_refine_correction, dim3(g2), dim3(b2), 0, st, l, l, Z, (const double*)w.eye.p, w.F.p,
+               w.lam.p, w.mx.p);
+    KOT_CHECK_LAUNCH();
+    KOT_LAUNCHED(1);
+  }
+  unsigned long long hm[3] = {0, 0, 0};
+  KOT_CUDA(cudaMemcpyAsync(hm, w.mx.p, sizeof(hm), cudaMemcpyDeviceToHost, st));
+  KOT_CUDA(cudaStreamSynchronize(st));
+  double me;
+  std::memcpy(&me, &hm[0], sizeof(double));
+  if (!(me <= kRefineStart)) return 0;
+  if (me <= w.refine_done) {   // X = I + E with |E| <= refine_done: the last step
+    k_rank_stride<<<cdiv(l, 32), dim3(32, 8), 0, st>>>(l, w.lam.p, 1, w.rank.p);
+    k_gather_vec<<<g2, b2, 0, st>>>(l, w.lam.p, w.F.p, l, w.rank.p, P, sig);
+    KOT_CHECK_LAUNCH();
+    KOT_LAUNCHED(2);
+    w.last_nb = (int)hm[2];
+    *diag = true;
+    return 1;
+  }
+  if (max_steps < 2) return 0;
+  // continue from X = I + E (F is overwritten by the next correction, so it is copied first)
+  w.X0.alloc(L2);
+  copy_mat(st, l, l, w.F.p, l, w.X0.p, l);
+  const int k = refine_sym_f64(st, l, Z, w.X0.p, P, sig, w, max_steps - 1, me);
+  return k > 0 ? k + 1 : 0;
+}
+
 }  // namespace
 
 int eig_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, double* P,
@@ -596,21 +647,21 @@ int eig_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, dou
   w.last_sweeps = 0;
   w.last_refine = 0;
   w.last_nb = -1;
+  w.last_trivial = false;
   if (max_refine > 0) {
     // No basis at all: try the identity first.  A nearly diagonal Z (the first projections of a
     // solve when the Gram matrix K is close to diagonal, small bandwidths) refines from it in a
     // few products, where cold Jacobi sweeps cost l - 1 grid-synchronised rounds each.
-    const double* eye = nullptr;
     if (!warm && !warm2) {
-      if (w.eye_l != l) {
-        w.eye.alloc((size_t)l * l);
-        fill(st, (size_t)l * l, 0.0, w.eye.p);
-        add_diag(st, l, 1.0, w.eye.p, l);
-        w.eye_l = l;
+      bool diag = false;
+      const int k = refine_from_identity(st, l, Z, P, sig, w, max_refine, &diag);
+      if (k > 0) {
+        w.last_refine = k;
+        w.last_trivial = diag;
+        return 0;
       }
-      eye = w.eye.p;
     }
-    for (const double* start : {warm, warm2, eye}) {
+    for (const double* start : {warm, warm2}) {
       if (!start) continue;
       const int k = refine_sym_f64(st, l, Z, start, P, sig, w, max_refine);
       if (k > 0) {
@@ -620,6 +671,7 @@ int eig_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, dou
     }
   }
   w.last_sweeps = jacobi_sym_f64(st, l, Z, warm, P, sig, w, max_sweeps, host_scal, ctas);
+  w.last_trivial = !warm && w.last_sweeps == 0;
   return w.last_sweeps;
 }
 

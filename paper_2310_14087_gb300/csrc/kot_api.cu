@@ -288,7 +288,7 @@ void eig_into(kot_ctx* C, const double* Z, EigSlot& e, const EigSlot* warm) {
     e.nb = C->hi[0];
   }
   e.valid = true;
-  e.trivial = wp == nullptr && C->jw.last_sweeps == 0 && C->jw.last_refine == 0;
+  e.trivial = wp == nullptr && C->jw.last_trivial;
   if (C->in_solve && !e.trivial) {
     KOT_CUDA(cudaMemcpyAsync(C->Plast.p, e.P.p, (size_t)l * l * sizeof(double), cudaMemcpyDeviceToDevice, C->st));
     C->plast_valid = true;

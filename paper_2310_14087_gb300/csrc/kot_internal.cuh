@@ -282,7 +282,8 @@ struct JacobiWork {
   DevBuf<double> rot;       // two rounds x lp/2 pairs x (c, s)
   DevBuf<int> pairs;        // lp
   DevBuf<int> rank;         // l
-  DevBuf<double> eye;       // l x l identity, the start of a refinement without a warm basis
+  DevBuf<double> eye;       // l x l identity: G of the first step of a refinement without a warm basis
+  DevBuf<double> X0;        // I + E after that step, the start of the rest
   int eye_l = 0;
   DevBuf<double> partial, scal;
   DevBuf<unsigned> bar;     // grid barrier [arrivals, generation]
@@ -293,9 +294,10 @@ struct JacobiWork {
   int threads_override = 0;        // > 0: threads per CTA of the Jacobi kernel (the autotuner's probes)
   int last_sweeps = 0;             // Jacobi sweeps of the last call
   int last_refine = 0;             // refinement steps of the last call (0: Jacobi was used)
+  bool last_trivial = false;       // no start basis, and Z was diagonal to the tolerance
   int last_nb = -1;                // eigenvalues <= 0 of a refined decomposition (-1: not counted)
   void release() {
-    for (DevBuf<double>* b : {&A, &V, &rot, &partial, &scal, &Xa, &Xb, &Y, &S, &G, &F, &lam, &eye}) b->release();
+    for (DevBuf<double>* b : {&A, &V, &rot, &partial, &scal, &Xa, &Xb, &Y, &S, &G, &F, &lam, &eye, &X0}) b->release();
     eye_l = 0;
     pairs.release();
     rank.release();
