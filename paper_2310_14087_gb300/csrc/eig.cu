@@ -639,6 +639,162 @@ int refine_from_identity(cudaStream_t st, int l, const double* Z, double* P, dou
   return k > 0 ? k + 1 : 0;
 }
 
+// ------------------------------------------------------------------ shared-memory FP32 Jacobi
+// Cold decompositions of small matrices (l <= kSmemJacobiMax): one CTA per matrix holds A and V in
+// FP32 in shared memory and runs parallel cyclic two-sided Jacobi (round-robin pairs, every 2 x 2
+// block of a round updated independently), synchronising with __syncthreads instead of a grid
+// barrier and issuing on the FP32 pipes (64x the FP64 rate of this part).  The basis it returns is
+// accurate to FP32 (orthogonality ~1e-6); the FP64 refinement takes it from there.
+constexpr int kSmemJacobiMax = 160;
+constexpr int kSmemJacobiSweeps = 20;
+constexpr int kSmemJacobiThreads = 1024;
+
+__global__ void __launch_bounds__(kSmemJacobiThreads, 1)
+    k_jacobi_smem_f32(int l, const double* __restrict__ Z, double* __restrict__ Vout,
+                      int* __restrict__ diag) {
+  extern __shared__ float jsm[];
+  const int lp = l + (l & 1), ld = lp + 1, np = lp / 2;
+  float* A = jsm;                          // lp x ld
+  float* V = A + (size_t)lp * ld;          // lp x ld
+  float* cs = V + (size_t)lp * ld;         // np x (c, s)
+  __shared__ float red[2][32];
+  __shared__ int done;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < lp * lp; e += nt) {
+    const int i = e / lp, j = e - i * lp;
+    A[i * ld + j] = (i < l && j < l) ? (float)(0.5 * (Z[(size_t)i * l + j] + Z[(size_t)j * l + i])) : 0.0f;
+    V[i * ld + j] = (i == j) ? 1.0f : 0.0f;
+  }
+  if (tid == 0) done = 0;
+  __syncthreads();
+  {
+    // an exactly diagonal Z (e.g. a multiple of I) is reported and left to the caller
+    int nz = 0;
+    for (int e = tid; e < lp * lp; e += nt) {
+      const int i = e / lp, j = e - i * lp;
+      nz |= (i != j && A[i * ld + j] != 0.0f);
+    }
+    nz = __syncthreads_or(nz);
+    if (tid == 0) *diag = nz ? 0 : 1;
+  }
+  const int nblk = np * (np + 1) / 2;      // pair blocks (P <= Q) of the upper triangle
+  for (int sweep = 0; sweep < kSmemJacobiSweeps; ++sweep) {
+    for (int r = 0; r < lp - 1; ++r) {
+      // angles of the round's pairs (symmetric Schur 2 x 2, Rutishauser's update of the diagonal)
+      if (tid < np) {
+        int p, q;
+        round_pair(lp, r, tid, p, q);
+        const float app = A[p * ld + p], aqq = A[q * ld + q], apq = A[p * ld + q];
+        float c = 1.0f, s = 0.0f;
+        if (apq != 0.0f) {
+          const float tau = (aqq - app) / (2.0f * apq);
+          const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+          c = rsqrtf(1.0f + t * t);
+          s = t * c;
+        }
+        cs[2 * tid] = c;
+        cs[2 * tid + 1] = s;
+      }
+      __syncthreads();
+      // A <- J^T A J on the blocks P <= Q (mirrored), V <- V J
+      for (int b = tid; b < nblk; b += nt) {
+        // block b of the upper triangle: row bi starts at bi np - bi (bi - 1) / 2
+        const float tn = (float)(2 * np + 1);
+        int bi = (int)(0.5f * (tn - sqrtf(tn * tn - 8.0f * (float)b)));
+        bi = max(0, min(bi, np - 1));
+        while (bi > 0 && bi * np - bi * (bi - 1) / 2 > b) --bi;
+        while (bi + 1 < np && (bi + 1) * np - (bi + 1) * bi / 2 <= b) ++bi;
+        const int bj = bi + (b - (bi * np - bi * (bi - 1) / 2));
+        int p1, q1, p2, q2;
+        round_pair(lp, r, bi, p1, q1);
+        round_pair(lp, r, bj, p2, q2);
+        const float c1 = cs[2 * bi], s1 = cs[2 * bi + 1], c2 = cs[2 * bj], s2 = cs[2 * bj + 1];
+        if (bi == bj) {
+          const float app = A[p1 * ld + p1], aqq = A[q1 * ld + q1], apq = A[p1 * ld + q1];
+          const float t = (c1 != 0.0f) ? s1 / c1 : 0.0f;
+          A[p1 * ld + p1] = app - t * apq;
+          A[q1 * ld + q1] = aqq + t * apq;
+          A[p1 * ld + q1] = 0.0f;
+          A[q1 * ld + p1] = 0.0f;
+        } else {
+          const float a11 = A[p1 * ld + p2], a12 = A[p1 * ld + q2];
+          const float a21 = A[q1 * ld + p2], a22 = A[q1 * ld + q2];
+          const float b11 = c2 * a11 - s2 * a12, b12 = s2 * a11 + c2 * a12;
+          const float b21 = c2 * a21 - s2 * a22, b22 = s2 * a21 + c2 * a22;
+          const float n11 = c1 * b11 - s1 * b21, n21 = s1 * b11 + c1 * b21;
+          const float n12 = c1 * b12 - s1 * b22, n22 = s1 * b12 + c1 * b22;
+          A[p1 * ld + p2] = n11;
+          A[q1 * ld + p2] = n21;
+          A[p1 * ld + q2] = n12;
+          A[q1 * ld + q2] = n22;
+          A[p2 * ld + p1] = n11;
+          A[p2 * ld + q1] = n21;
+          A[q2 * ld + p1] = n12;
+          A[q2 * ld + q1] = n22;
+        }
+      }
+      for (int e = tid; e < lp * np; e += nt) {
+        const int i = e / np, k = e - i * np;
+        int p, q;
+        round_pair(lp, r, k, p, q);
+        const float c = cs[2 * k], s = cs[2 * k + 1];
+        const float vp = V[i * ld + p], vq = V[i * ld + q];
+        V[i * ld + p] = c * vp - s * vq;
+        V[i * ld + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+    // off-diagonal against total Frobenius mass: FP32 has converged near 1e-7
+    float off = 0.0f, tot = 0.0f;
+    for (int e = tid; e < lp * lp; e += nt) {
+      const int i = e / lp, j = e - i * lp;
+      const float a = A[i * ld + j];
+      tot += a * a;
+      if (i != j) off += a * a;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if ((tid & 31) == 0) {
+      red[0][tid >> 5] = off;
+      red[1][tid >> 5] = tot;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float so = 0.0f, st = 0.0f;
+      for (int w = 0; w < (nt >> 5); ++w) {
+        so += red[0][w];
+        st += red[1][w];
+      }
+      done = (so <= 4e-14f * st) ? 1 : 0;
+    }
+    __syncthreads();
+    if (done) break;
+  }
+  for (int e = tid; e < l * l; e += nt) {
+    const int i = e / l, j = e - i * l;
+    Vout[(size_t)i * l + j] = (double)V[i * ld + j];
+  }
+}
+
+// FP32 eigenbasis of Z (l <= kSmemJacobiMax) into B (l x l, FP64, row-major, column j = vector j);
+// *diag (device) = 1 when Z was exactly diagonal.
+void jacobi_smem_f32(cudaStream_t st, int l, const double* Z, double* B, int* diag) {
+  const int lp = l + (l & 1);
+  const size_t smem = (2 * (size_t)lp * (lp + 1) + (size_t)lp) * sizeof(float);
+  static bool attr[64] = {};
+  int dev = 0;
+  KOT_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && !attr[dev]) {
+    const size_t mx = (2 * (size_t)(kSmemJacobiMax + 1) * (kSmemJacobiMax + 1) + kSmemJacobiMax + 1) * sizeof(float);
+    KOT_CUDA(cudaFuncSetAttribute(k_jacobi_smem_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
+    attr[dev] = true;
+  }
+  k_jacobi_smem_f32<<<1, kSmemJacobiThreads, smem, st>>>(l, Z, B, diag);
+  KOT_CHECK_LAUNCH();
+}
+
 }  // namespace
 
 int eig_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, double* P,
@@ -670,8 +826,42 @@ int eig_sym_f64(cudaStream_t st, int l, const double* Z, const double* warm, dou
       }
     }
   }
-  w.last_sweeps = jacobi_sym_f64(st, l, Z, warm, P, sig, w, max_sweeps, host_scal, ctas);
-  w.last_trivial = !warm && w.last_sweeps == 0;
+  // Still cold and small: an FP32 basis from the shared-memory Jacobi, refined to FP64 (or, where
+  // the refinement gives up, e.g. inside tight eigenvalue clusters, the start of the FP64 sweeps).
+  const double* start = warm;
+  if (!warm && !warm2 && max_refine > 0 && l >= 2 && l <= kSmemJacobiMax) {
+    w.B32.alloc((size_t)l * l);
+    w.flags.alloc(2);
+    jacobi_smem_f32(st, l, Z, w.B32.p, w.flags.p + 1);
+    int hdiag = 0;
+    KOT_CUDA(cudaMemcpyAsync(&hdiag, w.flags.p + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KOT_CUDA(cudaStreamSynchronize(st));
+    if (!hdiag) {
+      const int k = refine_sym_f64(st, l, Z, w.B32.p, P, sig, w, max_refine);
+      if (k > 0) {
+        w.last_refine = k;
+        return 0;
+      }
+      // Jacobi from a warm basis needs orthonormal columns: two Newton-Schulz steps
+      // B <- B (3 I - B^T B) / 2 take the FP32 basis's ~1e-6 loss of orthogonality to FP64 rounding
+      const size_t L2 = (size_t)l * l;
+      w.G.alloc(L2);
+      w.F.alloc(L2);
+      w.X0.alloc(L2);
+      double* b0 = w.B32.p;
+      double* b1 = w.X0.p;
+      for (int it = 0; it < 2; ++it) {
+        gemm_acc(st, w.oz, true, false, l, l, l, 1.0, b0, l, b0, l, nullptr, 0.0, w.G.p, l, G_SYM);
+        axpby(st, L2, -0.5, w.G.p, 0.0, nullptr, w.F.p);
+        add_diag(st, l, 1.5, w.F.p, l);
+        gemm_acc(st, w.oz, false, false, l, l, l, 1.0, b0, l, w.F.p, l, nullptr, 0.0, b1, l, 0);
+        std::swap(b0, b1);
+      }
+      start = b0;
+    }
+  }
+  w.last_sweeps = jacobi_sym_f64(st, l, Z, start, P, sig, w, max_sweeps, host_scal, ctas);
+  w.last_trivial = !start && w.last_sweeps == 0;
   return w.last_sweeps;
 }
 

@@ -284,6 +284,7 @@ struct JacobiWork {
   DevBuf<int> rank;         // l
   DevBuf<double> eye;       // l x l identity: G of the first step of a refinement without a warm basis
   DevBuf<double> X0;        // I + E after that step, the start of the rest
+  DevBuf<double> B32;       // l x l basis from the shared-memory FP32 Jacobi (l <= 160)
   int eye_l = 0;
   DevBuf<double> partial, scal;
   DevBuf<unsigned> bar;     // grid barrier [arrivals, generation]
@@ -297,7 +298,7 @@ struct JacobiWork {
   bool last_trivial = false;       // no start basis, and Z was diagonal to the tolerance
   int last_nb = -1;                // eigenvalues <= 0 of a refined decomposition (-1: not counted)
   void release() {
-    for (DevBuf<double>* b : {&A, &V, &rot, &partial, &scal, &Xa, &Xb, &Y, &S, &G, &F, &lam, &eye, &X0}) b->release();
+    for (DevBuf<double>* b : {&A, &V, &rot, &partial, &scal, &Xa, &Xb, &Y, &S, &G, &F, &lam, &eye, &X0, &B32}) b->release();
     eye_l = 0;
     pairs.release();
     rank.release();

@@ -232,3 +232,13 @@ def clustered_symmetric(l: int, seed: int, clusters: int = 6, width: float = 1e-
     Qm, _ = np.linalg.qr(rng.standard_normal((l, l)))
     Z = (Qm * lam) @ Qm.T
     return 0.5 * (Z + Z.T)
+
+
+def separated_symmetric(l: int, seed: int) -> np.ndarray:
+    """Symmetric l x l matrix with eigenvalues about 2/l apart over [-1, 1] in a random orthogonal
+    basis: no clusters, the easy case of a cold eigen-decomposition."""
+    rng = np.random.default_rng(seed)
+    lam = -1.0 + 2.0 * (np.arange(l) + 0.25 * rng.random(l)) / l
+    Qm, _ = np.linalg.qr(rng.standard_normal((l, l)))
+    Z = (Qm * lam) @ Qm.T
+    return 0.5 * (Z + Z.T)

@@ -32,11 +32,7 @@ def clustered_symmetric(l, seed, clusters=6, width=1e-9):
 
 def separated_symmetric(l, seed):
     """Symmetric l x l matrix with eigenvalues about 2/l apart in a random orthogonal basis."""
-    rng = np.random.default_rng(seed)
-    lam = -1.0 + 2.0 * (np.arange(l) + 0.25 * rng.random(l)) / l
-    Qm, _ = np.linalg.qr(rng.standard_normal((l, l)))
-    Z = (Qm * lam) @ Qm.T
-    return 0.5 * (Z + Z.T)
+    return wl.separated_symmetric(l, seed)
 
 
 def run_eig(ctx, Z, warm=None):
@@ -75,6 +71,20 @@ def test_cold_start_jacobi(l):
         assert refine == 0 and sweeps > 0
     else:
         assert (refine > 0 and sweeps == 0) or (refine == 0 and sweeps > 0)
+    check_decomposition(Z, P, sig)
+
+
+@pytest.mark.parametrize("l", [37, 100, 160, 161])
+def test_cold_start_small_l_uses_the_shared_memory_fp32_basis(l):
+    # separated spectrum in a random basis: up to l = 160 the shared-memory FP32 Jacobi supplies a
+    # basis that the FP64 refinement finishes (no FP64 sweep); above it the cooperative sweeps run
+    Z = separated_symmetric(l, seed=7 * l)
+    ctx = kot.Context(device=0)
+    P, sig, (sweeps, refine) = run_eig(ctx, Z)
+    if l <= 160:
+        assert sweeps == 0 and 1 <= refine <= 5
+    else:
+        assert refine == 0 and sweeps > 0
     check_decomposition(Z, P, sig)
 
 
