@@ -51,7 +51,9 @@ PROFILE_EVERY = 8   # events around one launch in 8 of that class (less perturba
 # l x l x l six-slice launch; None until a capture of the current kernel exists.
 # (gemm_oz, 300^3, six slices): 2344704 and 2340352 bytes read, 0 written, in the two captured
 # launches (profiles/oz_gemm_emulated_fp64_l300_l1024_l2048.md); algorithmic 2.30 MB of slices.
-ROOF_TRAFFIC = {("gemm_oz", "paper_d5_n1000_l300", 6): 2342528.0}
+# DRAM bytes per launch of the dominant kernel from an ncu capture (see profiles/), keyed by class,
+# workload and slices; None where the kernel changed since the counters were taken
+ROOF_TRAFFIC = {("gemm_oz", "paper_d5_n1000_l300", 6): 2341803.0}   # k_oz_gemm<128>
 
 
 def seed_of(rank: int, step: int) -> int:
@@ -233,9 +235,9 @@ def main():
                          "as many separate feature builds and solves")
     ap.add_argument("--batch", type=int, default=32, help="problems per batch (--method batch)")
     ap.add_argument("--autotune", action="store_true",
-                    help="run kot_autotune for l first (untimed); off by default: on the C2 shape "
-                         "its choice (12 splits, 128-wide tiles) measured 1.7%% faster inside the "
-                         "solve, but the bench line's DRAM traffic figure is for the default 64-wide tile")
+                    help="run kot_autotune for l first (untimed); off by default: its standalone "
+                         "timings favour more splits than the default, which measured best inside "
+                         "the solve (8 splits, 128-wide tiles at l = 300)")
     ap.add_argument("--max-iter", type=int, default=200,
                     help="outer-iteration cap of Algorithm 2 (lower it to time iterations at large l)")
     ap.add_argument("--workers", type=int, default=8, help="concurrent solves (--method batch)")

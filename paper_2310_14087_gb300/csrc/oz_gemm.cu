@@ -644,9 +644,11 @@ void gemm_oz(cudaStream_t st, OzWork& w, int M, int N, int K, const TcOperand& A
       ++np;
     }
   P.npairs = np;
-  // wide tiles for large products (twice the MMA work per 64-wide K step for 1.33x the bytes),
-  // unless the autotuner chose for this size bucket; w.bn_override (the tuner's probe) wins
-  int BNsel = (M >= 512 && N >= 512) ? 128 : 64;
+  // wide tiles from 256 up (twice the MMA work per 64-wide K step for 1.33x the bytes, and fewer,
+  // longer CTAs: inside the solve at l = 300, where the EG lane and the Newton step share the GPU,
+  // 128-wide tiles ran 4% faster than 64-wide ones), unless the autotuner chose for this size
+  // bucket; w.bn_override (the tuner's probe) wins
+  int BNsel = (M >= 256 && N >= 256) ? 128 : 64;
   const int tuned_bn = tuned_tile_width(device_index(), std::max(M, N), s);
   if (tuned_bn == 64 || tuned_bn == 128) BNsel = tuned_bn;
   if (w.bn_override == 64 || w.bn_override == 128) BNsel = w.bn_override;
