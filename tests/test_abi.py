@@ -43,6 +43,8 @@ def test_default_options_follow_the_paper(lib):
     assert o.cg_max_iter == 20
     assert (o.tau, o.kappa, o.theta0) == (0.1, 1.0, 1.0)
     assert o.precision == kot.FP64 and o.use_eg == 1
+    # library choices: products below 8e6 multiply-adds on the FP64 pipes, five refinement steps
+    assert o.tc_min_flops == 8e6 and o.eig_refine == 5
 
 
 def test_struct_layouts_match_header(lib):
