@@ -636,6 +636,43 @@ def test_mixed_solve_gates(name, tc_min_flops):
     assert np.abs(N(g) - gstar).max() <= 1e-5 * np.abs(gstar).max()
 
 
+@pytest.mark.parametrize("precision,obj_rel", [(kot.FP64, 1e-8), (kot.MIXED, 1e-6)])
+def test_rejected_newton_steps_take_the_eg_iterate(precision, obj_rel):
+    # with theta0 = 1e4 the first Newton steps are short (mu = theta ||R||), R(w~) loses to R(v)
+    # and Algorithm 2 takes the extragradient iterate (7 of the oracle's 30 iterations): this
+    # runs the EG lane's hand-over of v, R(v) and its eigenbasis to the Newton side
+    p = WORKLOADS["paper_d2_l50"]()
+    F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
+    ref = ko.ssn_solve(F, p.tol, ko.Options(theta0=1e4))
+    assert ref.converged and ref.eg_taken >= 1
+    ctx = kot.Context(device=0, precision=precision, theta0=1e4)
+    ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
+    g, X = Z(p.l), Z(p.l, p.l)
+    res = ctx.ssn_solve(p.tol, g, X)
+    assert res.status == kot.OK
+    assert res.eg_taken >= 1 and abs(res.eg_taken - ref.eg_taken) <= 2, (res.eg_taken, ref.eg_taken)
+    assert abs(res.iters - ref.iters) <= 3, (res.iters, ref.iters)
+    assert ko.residual(F, N(g), N(X)).norm <= p.tol * (1 + 1e-5)
+    assert res.objective == pytest.approx(ref.objective, rel=obj_rel)
+
+
+@pytest.mark.parametrize("precision", [kot.FP64, kot.MIXED])
+def test_plain_ssn_without_the_eg_safeguard(precision):
+    # use_eg = 0: every Newton step is taken (no EG lane); the oracle's plain SSN
+    p = WORKLOADS["paper_d2_l50"]()
+    F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
+    ref = ko.ssn_solve(F, p.tol, ko.Options(use_eg=False))
+    ctx = kot.Context(device=0, precision=precision, use_eg=0)
+    ctx.build_features(T(p.X), T(p.Y), T(p.Xf), T(p.Yf), p.sigma, p.lambda1, p.lambda2)
+    g, X = Z(p.l), Z(p.l, p.l)
+    res = ctx.ssn_solve(p.tol, g, X)
+    assert res.status == kot.OK and ref.converged
+    assert res.eg_taken == 0 and res.ssn_accepted == res.iters
+    assert abs(res.iters - ref.iters) <= 2, (res.iters, ref.iters)
+    assert ko.residual(F, N(g), N(X)).norm <= p.tol * (1 + 1e-5)
+    assert res.objective == pytest.approx(ref.objective, rel=1e-6)
+
+
 # The problems bench.py times (Sec. 5 regime, d = 5, n = 1000, l = 300, seeds 100..119: one
 # per step of a 20-step run).  With T acting on the symmetric part of its argument the oracle's
 # runs are insensitive to rounding (perturbing Q and z by up to 1e-7, or T's output by 1e-13,
