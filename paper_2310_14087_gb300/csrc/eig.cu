@@ -654,9 +654,12 @@ __global__ void __launch_bounds__(kSmemJacobiThreads, 1)
                       int* __restrict__ diag) {
   extern __shared__ float jsm[];
   const int lp = l + (l & 1), ld = lp + 1, np = lp / 2;
+  const int nblk = np * (np + 1) / 2;      // pair blocks (P <= Q) of the upper triangle
   float* A = jsm;                          // lp x ld
   float* V = A + (size_t)lp * ld;          // lp x ld
   float* cs = V + (size_t)lp * ld;         // np x (c, s)
+  int2* pq = reinterpret_cast<int2*>(cs + lp);          // np: the round's pairs
+  ushort2* blk = reinterpret_cast<ushort2*>(pq + np);  // nblk: (pair index P, pair index Q)
   __shared__ float red[2][32];
   __shared__ int done;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -664,6 +667,15 @@ __global__ void __launch_bounds__(kSmemJacobiThreads, 1)
     const int i = e / lp, j = e - i * lp;
     A[i * ld + j] = (i < l && j < l) ? (float)(0.5 * (Z[(size_t)i * l + j] + Z[(size_t)j * l + i])) : 0.0f;
     V[i * ld + j] = (i == j) ? 1.0f : 0.0f;
+  }
+  for (int b = tid; b < nblk; b += nt) {
+    // block b of the upper triangle: row bi starts at bi np - bi (bi - 1) / 2
+    const float tn = (float)(2 * np + 1);
+    int bi = (int)(0.5f * (tn - sqrtf(tn * tn - 8.0f * (float)b)));
+    bi = max(0, min(bi, np - 1));
+    while (bi > 0 && bi * np - bi * (bi - 1) / 2 > b) --bi;
+    while (bi + 1 < np && (bi + 1) * np - (bi + 1) * bi / 2 <= b) ++bi;
+    blk[b] = make_ushort2((unsigned short)bi, (unsigned short)(bi + (b - (bi * np - bi * (bi - 1) / 2))));
   }
   if (tid == 0) done = 0;
   __syncthreads();
@@ -677,7 +689,6 @@ __global__ void __launch_bounds__(kSmemJacobiThreads, 1)
     nz = __syncthreads_or(nz);
     if (tid == 0) *diag = nz ? 0 : 1;
   }
-  const int nblk = np * (np + 1) / 2;      // pair blocks (P <= Q) of the upper triangle
   for (int sweep = 0; sweep < kSmemJacobiSweeps; ++sweep) {
     for (int r = 0; r < lp - 1; ++r) {
       // angles of the round's pairs (symmetric Schur 2 x 2, Rutishauser's update of the diagonal)
@@ -694,20 +705,15 @@ __global__ void __launch_bounds__(kSmemJacobiThreads, 1)
         }
         cs[2 * tid] = c;
         cs[2 * tid + 1] = s;
+        pq[tid] = make_int2(p, q);
       }
       __syncthreads();
       // A <- J^T A J on the blocks P <= Q (mirrored), V <- V J
       for (int b = tid; b < nblk; b += nt) {
-        // block b of the upper triangle: row bi starts at bi np - bi (bi - 1) / 2
-        const float tn = (float)(2 * np + 1);
-        int bi = (int)(0.5f * (tn - sqrtf(tn * tn - 8.0f * (float)b)));
-        bi = max(0, min(bi, np - 1));
-        while (bi > 0 && bi * np - bi * (bi - 1) / 2 > b) --bi;
-        while (bi + 1 < np && (bi + 1) * np - (bi + 1) * bi / 2 <= b) ++bi;
-        const int bj = bi + (b - (bi * np - bi * (bi - 1) / 2));
-        int p1, q1, p2, q2;
-        round_pair(lp, r, bi, p1, q1);
-        round_pair(lp, r, bj, p2, q2);
+        const ushort2 bq = blk[b];
+        const int bi = bq.x, bj = bq.y;
+        const int2 pa = pq[bi], pb = pq[bj];
+        const int p1 = pa.x, q1 = pa.y, p2 = pb.x, q2 = pb.y;
         const float c1 = cs[2 * bi], s1 = cs[2 * bi + 1], c2 = cs[2 * bj], s2 = cs[2 * bj + 1];
         if (bi == bj) {
           const float app = A[p1 * ld + p1], aqq = A[q1 * ld + q1], apq = A[p1 * ld + q1];
@@ -735,8 +741,8 @@ __global__ void __launch_bounds__(kSmemJacobiThreads, 1)
       }
       for (int e = tid; e < lp * np; e += nt) {
         const int i = e / np, k = e - i * np;
-        int p, q;
-        round_pair(lp, r, k, p, q);
+        const int2 pk = pq[k];
+        const int p = pk.x, q = pk.y;
         const float c = cs[2 * k], s = cs[2 * k + 1];
         const float vp = V[i * ld + p], vq = V[i * ld + q];
         V[i * ld + p] = c * vp - s * vq;
@@ -782,12 +788,17 @@ __global__ void __launch_bounds__(kSmemJacobiThreads, 1)
 // *diag (device) = 1 when Z was exactly diagonal.
 void jacobi_smem_f32(cudaStream_t st, int l, const double* Z, double* B, int* diag) {
   const int lp = l + (l & 1);
-  const size_t smem = (2 * (size_t)lp * (lp + 1) + (size_t)lp) * sizeof(float);
+  // A, V (lp x (lp + 1) floats each), angles (lp floats), pairs (lp / 2 int2), block table
+  auto bytes = [](size_t lpv) {
+    const size_t npv = lpv / 2;
+    return (2 * lpv * (lpv + 1) + lpv) * sizeof(float) + npv * sizeof(int2) + npv * (npv + 1) / 2 * 4;
+  };
+  const size_t smem = bytes((size_t)lp);
   static bool attr[64] = {};
   int dev = 0;
   KOT_CUDA(cudaGetDevice(&dev));
   if (dev >= 0 && dev < 64 && !attr[dev]) {
-    const size_t mx = (2 * (size_t)(kSmemJacobiMax + 1) * (kSmemJacobiMax + 1) + kSmemJacobiMax + 1) * sizeof(float);
+    const size_t mx = bytes((size_t)kSmemJacobiMax);
     KOT_CUDA(cudaFuncSetAttribute(k_jacobi_smem_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
     attr[dev] = true;
   }
