@@ -82,8 +82,9 @@ typedef struct {
                               finished with them if short), FP64-accuracy CG products below
                               it (default 1e-4)                                            */
   int batch_workers;       /* kot_batch_solve: problems solved concurrently (0 = 4)        */
-  int eig_refine;          /* eigen-decompositions with a warm basis (the previous one of the
-                              same sequence): at most this many refinement steps from it
+  int eig_refine;          /* eigen-decompositions: at most this many refinement steps from a
+                              start basis (the previous one of the same sequence, then the
+                              slot's own previous one, or the identity when there is none)
                               before falling back to Jacobi sweeps; 0 = always Jacobi (default 5) */
   int schur_solver;        /* Krylov method for the Schur system of Algorithm 1 (Sec. 4.3 names
                               both): 0 = conjugate gradients (default), 1 = symmetric QMR
@@ -112,7 +113,7 @@ typedef struct {
   double seconds;          /* wall time of the call                                      */
   int eig_calls;           /* symmetric eigen-decompositions performed by the solve      */
   int eig_sweeps;          /* Jacobi sweeps summed over them                             */
-  int eig_refined;         /* decompositions finished by refining the warm basis         */
+  int eig_refined;         /* decompositions finished by refinement (no FP64 sweep)      */
   int eig_refine_steps;    /* refinement steps summed over them                          */
 } kot_result;
 
@@ -247,9 +248,11 @@ kot_status kot_bootstrap_solve(kot_ctx* ctx, int B, int n, const double* Xs, con
  * warm (may be NULL): an orthogonal l x l basis (row-major, orthonormal columns) close to the
  * eigenbasis, e.g. the one of a nearby matrix.  With it the library first refines warm into
  * the eigenbasis (Ogita-Aishima iteration, at most opt.eig_refine steps of FP64 products) and
- * rebuilds by Jacobi sweeps from warm when that does not converge; without it, the same from
- * the identity (a nearly diagonal Z then needs no sweeps).  info (host, may be NULL) receives
- * {Jacobi sweeps, refinement steps} of the call.
+ * rebuilds by Jacobi sweeps from warm when that does not converge.  Without it the refinement
+ * starts from the identity (a nearly diagonal Z then needs no sweeps); failing that, for
+ * l <= 160 from an FP32 basis computed by Jacobi in one CTA's shared memory, and the FP64
+ * sweeps, if still needed, start from that basis orthonormalised.  info (host, may be NULL)
+ * receives {FP64 Jacobi sweeps, refinement steps} of the call.
  * Pointers follow the context's pointer mode.  No features are needed.  KOT_ERR_TIMEOUT if a
  * bounded wait of the cooperative Jacobi kernel gave up, KOT_ERR_NO_CONVERGENCE if the sweeps
  * did not converge. */
