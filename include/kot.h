@@ -52,7 +52,10 @@ typedef enum {
                          products (residual, projection, EG, eigenbasis refinement, Newton
                          right-hand side and check) emulated with six fixed-point BF16
                          slices; the Jacobian products inside CG with three (about FP32
-                         accuracy); FP64 features, Jacobi rotations, vectors and stop test  */
+                         accuracy), or exact FP64 kernels with at most 32 carried rows;
+                         products below opt.tc_min_flops on the FP64 pipes; FP64 features,
+                         Jacobi rotations (a cold start up to l = 160 in FP32, refined to
+                         FP64), vectors and stop test                                   */
 } kot_precision;
 
 /* Algorithm constants.  Defaults (kot_default_options): the values of Sec. 5 for alpha1,
