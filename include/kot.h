@@ -47,7 +47,8 @@ typedef enum {
 } kot_status;
 
 typedef enum {
-  KOT_FP64 = 0,       /* every step in FP64                                             */
+  KOT_FP64 = 0,       /* every step in FP64 (a cold eigen-decomposition up to l = 160
+                         starts from an FP32 shared-memory Jacobi basis, refined to FP64) */
   KOT_MIXED = 1       /* every O(l^3) product on the tcgen05 tensor cores: FP64-accuracy
                          products (residual, projection, EG, eigenbasis refinement, Newton
                          right-hand side and check) emulated with six fixed-point BF16
