@@ -422,6 +422,25 @@ def test_eg_step_fixes_a_solution():
         np.testing.assert_allclose(X1, r.X, atol=1e-9)
 
 
+def test_rejected_steps_reach_the_same_optimum():
+    # Algorithm 2's acceptance test: with theta0 = 1e4 the first Newton steps are short and the
+    # extragradient iterate wins several times; without the safeguard every Newton step is taken.
+    # The optimum is unique (the objective is strongly convex in gamma), so all three runs must
+    # agree on it to the accuracy a residual of 1e-6 gives (runs stopped at 1e-6 differ from the
+    # optimum by up to ~2e-5 in f on these problems), and the counts must add up.
+    p = wl.paper_regime(seed=2, d=2, n=100, l=50)
+    F = ko.build_features(p.X, p.Y, p.Xf, p.Yf, p.sigma, p.lambda1, p.lambda2)
+    base = ko.ssn_solve(F, 1e-6)
+    slow = ko.ssn_solve(F, 1e-6, ko.Options(theta0=1e4))
+    plain = ko.ssn_solve(F, 1e-6, ko.Options(use_eg=False))
+    assert base.converged and slow.converged and plain.converged
+    assert slow.eg_taken >= 1 and slow.ssn_accepted + slow.eg_taken == slow.iters
+    assert plain.eg_taken == 0 and plain.ssn_accepted == plain.iters
+    for r in (slow, plain):
+        assert r.objective == pytest.approx(base.objective, rel=1e-4)
+        np.testing.assert_allclose(r.gamma, base.gamma, atol=1e-3 * np.abs(base.gamma).max())
+
+
 def test_potentials_reproduce_the_estimator():
     # <u, w_mu>_H = (1/n) sum_j u(x_j) (reproducing property), so averaging the potentials over
     # the samples must give OT-hat = q^2/(2 l2) - sum_i gamma_i (w_mu(xf_i) + w_nu(yf_i))/(2 l2)
